@@ -1,0 +1,397 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (``oracle/``) against something other than itself:
+a second statement of the method from another part of the paper, a closed form,
+a textbook value, an exact special case, or the continuum equations the scheme
+must reproduce (Eqs. 5-6 of arXiv:2208.03562).  No CUDA code is involved.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import matrix_form as MF
+from oracle import stepper as S
+from paper_2208_03562_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+R_SET = [0.25, 0.5, 1.0, 1.6, 2.0]
+GAMMA_SET = [0.05, 0.1, 0.5, 1.0]
+
+
+def _random_node(g, p):
+    rho = g.uniform(0.95, 1.05)
+    ux, uy = 0.03 * g.standard_normal(2)
+    f = S.equilibrium(p, rho, ux, uy) + 1e-3 * g.standard_normal(9)
+    dx, dy = 1e-3 * g.standard_normal(2)
+    return f, dx, dy
+
+
+# --------------------------------------------------------------------------
+# transcription: App. A step list (oracle-A) == matrix form (oracle-B)
+
+@pytest.mark.parametrize("r", R_SET)
+@pytest.mark.parametrize("gamma", GAMMA_SET)
+def test_step_list_equals_matrix_form(r, gamma):
+    """Eq. 10-equivalent-centralmoment with the printed F matrix and the
+    Sec. 3 coefficients (Eqs. 38-48) gives the same post-collision populations
+    as the Appendix A step list, for random states, forces and rates."""
+    g = I.rng(1000 + int(100 * r) + int(1000 * gamma))
+    for _ in range(40):
+        p = S.OracleParams(nx=1, ny=1, r=r, gamma=gamma, nu=g.uniform(1e-3, 0.1),
+                           omega_xi=g.uniform(0.5, 1.8), omega_21=g.uniform(0.5, 1.8),
+                           omega_12=g.uniform(0.5, 1.8), omega_22=g.uniform(0.5, 1.8),
+                           fx=1e-4 * g.standard_normal(), fy=1e-4 * g.standard_normal())
+        f, dx, dy = _random_node(g, p)
+        fa, da = S.collide_node(p, f, dx, dy)
+        fb, db = MF.collide(f, r, gamma, S.omega_nu(p), dx, dy, p.fx, p.fy,
+                            omega_3=p.omega_xi, omega_6=p.omega_21, omega_7=p.omega_12,
+                            omega_8=p.omega_22)
+        scale = np.max(np.abs(fa))
+        assert np.max(np.abs(fa - fb)) <= 1e-12 * scale
+        assert np.allclose(da, db, rtol=1e-9, atol=1e-15)
+
+
+def test_matrix_identities():
+    """F(u) F(-u) = I (Sec. 4.2); Q = S P (Eq. QandPrelation); T = B Q
+    (Eq. TandQrelation) with T from Eqs. 7-8; the printed F equals B F_bare B^-1
+    for the binomial transform of the bare moments."""
+    g = I.rng(7)
+    for r in R_SET:
+        Q, P, Sm, B = MF.Q_matrix(r), MF.P_matrix(), MF.S_matrix(r), MF.B_matrix()
+        assert np.allclose(Q, Sm @ P, atol=1e-15)
+        T = MF.T_basis(MF.EX, r * MF.EYB)
+        assert np.allclose(T, B @ Q, atol=1e-15)
+    for _ in range(20):
+        ux, uy = 0.2 * g.standard_normal(2)
+        Fm = MF.F_matrix(ux, uy)
+        assert np.allclose(Fm @ MF.F_matrix(-ux, -uy), np.eye(9), atol=1e-14)
+        # central moments of random populations computed by definition (Eq. 9B)
+        f = g.uniform(0, 1, 9)
+        r = 0.5
+        ex, ey = MF.EX, r * MF.EYB
+        cx, cy = ex - ux, ey - uy
+        central_bare = np.array([np.sum(f * cx ** m * cy ** n) for m, n in
+                                 [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2), (1, 1), (2, 1), (1, 2), (2, 2)]])
+        n = MF.B_matrix() @ MF.Q_matrix(r) @ f
+        assert np.allclose(Fm @ n, MF.B_matrix() @ central_bare, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# rest state, equilibrium, bounce-back
+
+def test_rest_weights_textbook_at_r1():
+    with open(os.path.join(GOLDEN, "d2q9_square_weights.json")) as fh:
+        gold = json.load(fh)
+    w = S.rest_weights(S.OracleParams(nx=1, ny=1, r=1.0))
+    assert np.allclose(36 * w, gold["weights_times_36"], atol=1e-14)
+
+
+@pytest.mark.parametrize("r", R_SET)
+def test_rest_weights_moments(r):
+    """w(r) are the populations whose moments are the rest equilibria of
+    Eq. 12 at u = 0: sum 1, <ex^2> = <ey^2> = q^2/3, <ex^2 ey^2> = (q^2/3)^2,
+    all odd moments zero; all weights positive."""
+    w = S.rest_weights(S.OracleParams(nx=1, ny=1, r=r))
+    ex, ey = MF.EX, r * MF.EYB
+    c2 = min(1.0, r) ** 2 / 3
+    assert abs(w.sum() - 1) < 1e-14
+    assert abs(np.sum(w * ex ** 2) - c2) < 1e-14
+    assert abs(np.sum(w * ey ** 2) - c2) < 1e-14
+    assert abs(np.sum(w * ex ** 2 * ey ** 2) - c2 * c2) < 1e-14
+    for m in (ex, ey, ex * ey, ex ** 2 * ey, ex * ey ** 2):
+        assert abs(np.sum(w * m)) < 1e-14
+    assert np.all(w > 0)
+
+
+@pytest.mark.parametrize("r", R_SET)
+def test_equilibrium_moments(r):
+    """f^eq(rho, u) reproduces the raw-moment equilibria of Eq. 12 by direct
+    summation (Eq. 9A) on the rectangular velocities."""
+    g = I.rng(11)
+    for gamma in GAMMA_SET:
+        p = S.OracleParams(nx=1, ny=1, r=r, gamma=gamma)
+        rho, ux, uy = 1 + 0.02 * g.standard_normal(), *(0.05 * g.standard_normal(2))
+        f = S.equilibrium(p, rho, ux, uy)
+        ex, ey = MF.EX, r * MF.EYB
+        c2 = min(1.0, r) ** 2 / 3
+        mom = lambda m, n: float(np.sum(f * ex ** m * ey ** n))
+        assert math.isclose(mom(0, 0), rho, rel_tol=1e-13)
+        assert math.isclose(mom(1, 0), rho * ux, rel_tol=1e-12)
+        assert math.isclose(mom(2, 0), c2 * rho + rho * ux ** 2 / gamma, rel_tol=1e-12)
+        assert math.isclose(mom(0, 2), c2 * rho + rho * uy ** 2 / gamma, rel_tol=1e-12)
+        assert math.isclose(mom(1, 1), rho * ux * uy / gamma, rel_tol=1e-11)
+        assert math.isclose(mom(2, 1), rho * (c2 + ux ** 2 / gamma ** 2) * uy, rel_tol=1e-11)
+        assert math.isclose(mom(1, 2), rho * (c2 + uy ** 2 / gamma ** 2) * ux, rel_tol=1e-11)
+
+
+@pytest.mark.parametrize("r", R_SET)
+def test_wall_correction_momentum(r):
+    """The bounce-back correction of a wall moving with u_w carries the wall
+    momentum: sum_i (f^eq_i(u_w) - f^eq_ibar(u_w)) e_i / 2 = rho_w u_w; at r = 1
+    the diagonal term is the textbook 2 w_5 rho (e_5 . u_w) / c_s^2 = U / 6."""
+    U = 0.05
+    p = S.OracleParams(nx=1, ny=1, r=r)
+    feq = S.equilibrium(p, 1.0, U, 0.0)
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    odd = np.array([feq[i] - feq[opp[i]] for i in range(9)]) / 2
+    ex, ey = MF.EX, r * MF.EYB
+    assert abs(np.sum(odd * ex) - U) < 1e-15
+    assert abs(np.sum(odd * ey)) < 1e-15
+    if r == 1.0:
+        assert abs((feq[5] - feq[7]) - U / 6) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# conservation and exact special cases of the collision
+
+@pytest.mark.parametrize("r", R_SET)
+@pytest.mark.parametrize("gamma", GAMMA_SET)
+def test_collision_conserves_mass_and_momentum(r, gamma):
+    """k~00 = k00 and k~10 = k10 + F/gamma (App. A relaxation with the source of
+    Eq. 13-central): mass is conserved and momentum gains F/gamma per step."""
+    g = I.rng(2000 + int(10 * r) + int(100 * gamma))
+    for _ in range(30):
+        p = S.OracleParams(nx=1, ny=1, r=r, gamma=gamma, nu=g.uniform(1e-3, 0.1),
+                           fx=1e-4 * g.standard_normal(), fy=1e-4 * g.standard_normal())
+        f, dx, dy = _random_node(g, p)
+        ft, _ = S.collide_node(p, f, dx, dy)
+        ex, ey = MF.EX, r * MF.EYB
+        assert abs(ft.sum() - f.sum()) < 1e-14
+        assert abs(np.sum(ft * ex) - np.sum(f * ex) - p.fx / gamma) < 1e-14
+        assert abs(np.sum(ft * ey) - np.sum(f * ey) - p.fy / gamma) < 1e-14
+
+
+@pytest.mark.parametrize("r", R_SET)
+def test_full_relaxation_is_product_form(r):
+    """gamma = 1, every rate 1, corrections off: the post-collision state is the
+    equilibrium of Eq. 14, whose central moments factor (k20 = k02 = c^2,
+    k22 = c^4, odd ones 0).  On three velocities per axis this is the unique
+    product f_i = rho phi_x(e_ix) phi_y(e_iy) of 1-D distributions with mean u
+    and variance q^2/3."""
+    g = I.rng(31)
+    c2 = min(1.0, r) ** 2 / 3
+    for _ in range(20):
+        p = S.OracleParams(nx=1, ny=1, r=r, gamma=1.0, nu=c2 / 2, corrections=0)
+        assert abs(S.omega_nu(p) - 1.0) < 1e-14
+        f = S.rest_weights(p) + 2e-3 * g.standard_normal(9)
+        ft, (rho, ux, uy, _, _) = S.collide_node(p, f)
+        phx = {0: 1 - c2 - ux ** 2, 1: (c2 + ux ** 2 + ux) / 2, -1: (c2 + ux ** 2 - ux) / 2}
+        phy = {0: 1 - (c2 + uy ** 2) / r ** 2, 1: (c2 + uy ** 2 + r * uy) / (2 * r ** 2),
+               -1: (c2 + uy ** 2 - r * uy) / (2 * r ** 2)}
+        expect = np.array([rho * phx[int(a)] * phy[int(b)] for a, b in zip(MF.EX, MF.EYB)])
+        assert np.allclose(ft, expect, atol=1e-15)
+
+
+def test_square_lattice_reduction():
+    """r = 1, gamma = 1: q = 1, U_gamma c^2 - 1 = 0, 3 c^2 - 1 = 3 c^2 - r^2 = 0,
+    Q_gamma = 0 -- every density-gradient term, every grid-anisotropy term and
+    every off-diagonal correction vanishes (Sec. 3.4), so the collision does not
+    depend on the density gradient at all and equals the square-lattice
+    non-orthogonal central-moment scheme with only the cubic correction left."""
+    g = I.rng(41)
+    for _ in range(20):
+        p = S.OracleParams(nx=1, ny=1, r=1.0, gamma=1.0, nu=g.uniform(1e-3, 0.1))
+        f, _, _ = _random_node(g, p)
+        a, _ = S.collide_node(p, f, 0.0, 0.0)
+        b, _ = S.collide_node(p, f, 0.3, -0.2)
+        assert np.max(np.abs(a - b)) < 1e-16
+
+
+# --------------------------------------------------------------------------
+# density-gradient stencil (reading A1)
+
+@pytest.mark.parametrize("r", [0.5, 2.0])
+def test_density_gradient_exact_on_linear_field(r):
+    nx, ny = 7, 6
+    o = S.Oracle(S.OracleParams(nx=nx, ny=ny, r=r))
+    X, Y = I.node_coords(nx, ny, r)
+    a, b = 0.013, -0.021
+    o.set_rho(1.0 + a * X + b * Y)
+    for y in range(1, ny - 1):
+        for x in range(1, nx - 1):
+            dx, dy = o.density_gradient(x, y)
+            assert abs(dx - a) < 1e-14 and abs(dy - b) < 1e-14
+    # zero normal gradient at a wall: ghost = nearest fluid node
+    o.set_rho(1.0 + a * X)
+    dx, dy = o.density_gradient(0, 2)
+    assert abs(dx - a / 2) < 1e-14 and abs(dy) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# continuum behaviour: viscosity, grid anisotropy, Galilean corrections
+
+def _mode_rate(o, every, nblocks, project):
+    ts, amps = [], []
+    for _ in range(nblocks):
+        o.step(every)
+        ts.append(o.t)
+        amps.append(project(o.fields()))
+    ts, amps = np.array(ts), np.array(amps)
+    sl = slice(len(ts) // 4, None)
+    return -np.polyfit(ts[sl], np.log(amps[sl]), 1)[0]
+
+
+def shear_wave_rate_error(nx, ny, r, gamma, nu_over_gamma, along):
+    p = S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu_over_gamma * gamma, bc=S.BC_PERIODIC)
+    o = S.Oracle(p)
+    o.init_fields(*I.shear_wave(nx, ny, r, 1e-4, along))
+    X, Y = I.node_coords(nx, ny, r)
+    if along == "y":
+        basis, k, comp = np.sin(2 * np.pi * Y / (ny * r)), 2 * np.pi / (ny * r), 1
+    else:
+        basis, k, comp = np.sin(2 * np.pi * X / nx), 2 * np.pi / nx, 2
+    rate = _mode_rate(o, 20, 20, lambda fl: np.sum(fl[comp] * basis) / np.sum(basis * basis))
+    return rate / (nu_over_gamma * k * k) - 1.0
+
+
+@pytest.mark.parametrize("r", [0.5, 2.0])
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_shear_wave_viscosity(r, gamma):
+    """A shear wave decays as exp(-(nu/gamma) k^2 t): Eq. 6 divides the viscous
+    stress by gamma, with nu = gamma q^2 c_s*^2 (1/omega_nu - 1/2) (Eq.
+    transport-coefficients).  Checked along both axes; the error is second
+    order in the grid spacing."""
+    e32 = shear_wave_rate_error(4, 32, r, gamma, 0.05, "y")
+    e64 = shear_wave_rate_error(4, 64, r, gamma, 0.05, "y")
+    assert abs(e32) < 5e-3 and abs(e64) < 1.5e-3
+    assert abs(e32) / abs(e64) > 3.0
+    ex = shear_wave_rate_error(32, 4, r, gamma, 0.05, "x")
+    assert abs(ex) < 5e-3
+
+
+def taylor_green_rate_error(nx, ny, r, gamma, nu_over_gamma, u0=0.0, corrections=1):
+    p = S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu_over_gamma * gamma,
+                       bc=S.BC_PERIODIC, corrections=corrections)
+    o = S.Oracle(p)
+    o.init_fields(*I.taylor_green(nx, ny, r, 1e-4, u0))
+
+    def amp(fl):
+        F = np.fft.fft2(fl[2])
+        return np.abs(F[1, 1]) + np.abs(F[-1, 1]) + np.abs(F[1, -1]) + np.abs(F[-1, -1])
+
+    rate = _mode_rate(o, 20, 30, amp)
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / (ny * r)
+    return rate / (nu_over_gamma * (kx * kx + ky * ky)) - 1.0
+
+
+@pytest.mark.parametrize("r,nx,ny", [(0.5, 32, 64), (2.0, 32, 16)])
+@pytest.mark.parametrize("gamma", [0.5, 1.0])
+def test_taylor_green_grid_anisotropy(r, nx, ny, gamma):
+    """A Taylor-Green vortex has normal strain (d_x u_x = -d_y u_y != 0), so on a
+    rectangular grid it decays at the isotropic rate (nu/gamma) |k|^2 only if
+    the grid-anisotropy corrections (Eqs. 38-39 with the local strain rates of
+    Eq. 48) are applied.  Planted omission: corrections off -> far off."""
+    assert abs(taylor_green_rate_error(nx, ny, r, gamma, 0.05)) < 3e-3
+    assert abs(taylor_green_rate_error(nx, ny, r, gamma, 0.05, corrections=0)) > 0.5
+
+
+@pytest.mark.parametrize("gamma,u0", [(1.0, 0.1), (0.5, 0.05), (0.25, 0.03)])
+def test_taylor_green_galilean_invariance(gamma, u0):
+    """With a uniform background flow u0 the decay rate of the advected vortex
+    must stay (nu/gamma)|k|^2; on the square lattice (r = 1) only the cubic
+    non-Galilean-invariant corrections (P_gamma, Q_gamma terms, Eqs. 38-40) are
+    active.  Planted omission: corrections off -> error of a few percent."""
+    assert abs(taylor_green_rate_error(32, 32, 1.0, gamma, 0.02, u0)) < 2e-3
+    assert abs(taylor_green_rate_error(32, 32, 1.0, gamma, 0.02, u0, corrections=0)) > 1.5e-2
+
+
+# --------------------------------------------------------------------------
+# walls: Couette and Poiseuille on rectangular grids
+
+@pytest.mark.parametrize("r", [0.5, 2.0])
+@pytest.mark.parametrize("gamma,U", [(1.0, 0.05), (0.1, 0.002)])
+def test_couette_exact(r, gamma, U):
+    """Half-way bounce-back with the moving-wall correction gives the exact
+    linear Couette profile u_x = U (j + 1/2) / ny.  (With the corrections on, the
+    local strain-rate estimate next to the moving wall adds an error that grows
+    like a high power of U/gamma; the pin uses U/gamma <= 0.05.)"""
+    ny = 16
+    p = S.OracleParams(nx=4, ny=ny, r=r, gamma=gamma, nu=0.05 * gamma, u_lid=U, bc=S.BC_CHANNEL)
+    o = S.Oracle(p)
+    o.run(1e-15, 400000)
+    _, ux, uy = o.fields()
+    exact = U * (np.arange(ny) + 0.5) / ny
+    assert np.max(np.abs(ux - exact[:, None])) / U < 2e-7
+    assert np.max(np.abs(uy)) / U < 1e-10
+
+
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_couette_exact_without_corrections(gamma):
+    """The bare scheme (Eq. 14 equilibria) reproduces Couette flow to round-off
+    at any U/gamma: the wall treatment itself is exact."""
+    ny, U = 16, 0.05
+    p = S.OracleParams(nx=4, ny=ny, r=0.5, gamma=gamma, nu=0.05 * gamma, u_lid=U,
+                       bc=S.BC_CHANNEL, corrections=0)
+    o = S.Oracle(p)
+    o.run(1e-15, 400000)
+    _, ux, _ = o.fields()
+    exact = U * (np.arange(ny) + 0.5) / ny
+    assert np.max(np.abs(ux - exact[:, None])) / U < 1e-11
+
+
+def poiseuille_error(ny, r, gamma, nu=0.05, umax=0.02):
+    H = ny * r
+    fx = 8 * nu * umax / H ** 2
+    p = S.OracleParams(nx=2, ny=ny, r=r, gamma=gamma, nu=nu, fx=fx, bc=S.BC_CHANNEL)
+    o = S.Oracle(p)
+    o.run(1e-13, 2000000)
+    rho, ux, _ = o.fields()
+    y = (np.arange(ny) + 0.5) * r
+    exact = fx * y * (H - y) / (2 * nu * rho[:, 0])
+    return np.linalg.norm(ux[:, 0] - exact) / np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("r", [0.5, 2.0])
+@pytest.mark.parametrize("gamma", [1.0, 0.5])
+def test_poiseuille_second_order(r, gamma):
+    """Body-force channel flow: the gamma-scaled sources (Eq. 13-central) and
+    the half-force velocity shift give the parabola F y (H - y) / (2 rho nu)
+    independent of gamma, converging at second order."""
+    e16, e32 = poiseuille_error(16, r, gamma), poiseuille_error(32, r, gamma)
+    assert e32 < 6e-3
+    assert 3.8 < e16 / e32 < 4.2
+
+
+# --------------------------------------------------------------------------
+# closed cavity: mass, preconditioning
+
+def test_cavity_mass_conserved():
+    p = S.OracleParams(nx=20, ny=14, r=0.5, gamma=0.25, nu=0.01, u_lid=0.02)
+    o = S.Oracle(p)
+    m0 = o.total_mass()
+    o.step(2000)
+    assert abs(o.total_mass() - m0) < 1e-12 * m0
+
+
+def test_preconditioning_keeps_steady_state_and_cuts_steps():
+    """gamma < 1 reaches the same steady state (Eqs. 5-6 at steady state do not
+    contain gamma) in fewer steps (Sec. 5.2).  Compared away from the two
+    singular lid corners, where the discretisation error depends on omega_nu."""
+    nx, ny, r, U, Re = 24, 24, 1.0, 0.02, 20.0
+    nu = U * ny * r / Re
+    out = {}
+    for gamma in (1.0, 0.25):
+        o = S.Oracle(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=U))
+        steps, res = o.run(1e-11, 400000)
+        assert res < 1e-11
+        out[gamma] = (steps, o.fields())
+    (s1, f1), (s2, f2) = out[1.0], out[0.25]
+    assert s2 < s1 / 2.5
+    d = np.hypot(f1[1] - f2[1], f1[2] - f2[2]) / U
+    assert d[: ny - 4].max() < 1e-2
+    assert d[4: ny - 6, 4: nx - 4].max() < 5e-3
+
+
+# --------------------------------------------------------------------------
+# workload geometry against the paper's printed grids
+
+def test_paper_grid_geometry():
+    with open(os.path.join(GOLDEN, "paper_grids.json")) as fh:
+        gold = json.load(fh)
+    for c in gold["cases"]:
+        cav = I.Cavity(c["nx"], c["ny"], c["r"], 1.0, 100.0, 0.01)
+        assert abs(cav.height / cav.nx - c["AR"]) < 0.005 * c["AR"], c["where"]
