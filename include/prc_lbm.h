@@ -1,0 +1,217 @@
+/*
+ * prc_lbm.h -- C ABI of the GB300 PRC-LBM library (libprc_lbm.so).
+ *
+ * The library advances the preconditioned rectangular central-moment lattice
+ * Boltzmann method (PRC-LBM) of E. Yahia & K. N. Premnath, arXiv:2208.03562,
+ * on the D2Q9 lattice with grid aspect ratio r = dy/dx and preconditioning
+ * parameter gamma.  One time step is the fused per-node update
+ *     pull-stream (App. A, streaming) with half-way bounce-back walls and a
+ *     moving lid  ->  raw moments (Eq. 62), scaling S, central moments F
+ *     (Sec. 4.2)  ->  preconditioned equilibria with the grid-anisotropy and
+ *     cubic-velocity corrections (Eqs. 14, 30-40; App. A), local strain rates
+ *     (Eqs. 43-48)  ->  relaxation (App. A)  ->  F^-1, S^-1, P^-1 (Eq. 72),
+ * executed by hand-written sm_103a CUDA kernels.  No call falls back to the
+ * CPU.
+ *
+ * Units: lattice units dx = dt = 1, dy = r.  Node (i, j), i in [0, nx) along
+ * x, j in [0, ny) along y, sits at x = i + 1/2, y = (j + 1/2) r.
+ * Directions 0..8: rest, E, N, W, S, NE, NW, SW, SE (Eq. 3).
+ *
+ * Conventions for every entry point:
+ *  - every call returns an lbm_status and never aborts, traps or exits;
+ *  - asynchronous failures (divergence, a bounded wait that ran out) are
+ *    reported by the next call that synchronises (lbm_run, lbm_residual,
+ *    lbm_info, lbm_fields, lbm_sync ...);
+ *  - a handle is not thread-safe; distinct handles are independent;
+ *  - "device" pointers are CUDA device addresses on the handle's device,
+ *    "host" pointers are ordinary (pageable or pinned) host memory;
+ *  - population arrays are [9][ny][nx] (x fastest) of FP64 *full*
+ *    populations f_i (not the internal shifted storage);
+ *  - field arrays are [ny][nx] FP64.
+ */
+#ifndef PRC_LBM_H
+#define PRC_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_s *lbm_t;
+
+typedef enum {
+    LBM_F64 = 0, /* FP64 storage, FP64 collision                          */
+    LBM_F32 = 1, /* FP32 storage of f_i - w_i rho0, FP32 collision        */
+    LBM_F16 = 2  /* FP16 storage of f_i - w_i rho0, FP32 collision        */
+} lbm_dtype;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,        /* bad argument or parameter                       */
+    LBM_ENOMEM = 2,        /* device allocation failed / workspace too small  */
+    LBM_ECUDA = 3,         /* a CUDA runtime call failed (see lbm_last_error) */
+    LBM_EDIVERGED = 4,     /* non-finite residual or mass                     */
+    LBM_ETIMEOUT = 5,      /* a bounded device wait ran out                   */
+    LBM_ENOTCONVERGED = 6  /* lbm_run hit max_steps above tol                 */
+} lbm_status;
+
+typedef enum {
+    LBM_BC_CAVITY = 0,   /* walls at x = 0, x = nx, y = 0; lid (u_lid, 0) at y = ny r */
+    LBM_BC_CHANNEL = 1,  /* periodic in x; wall at y = 0; wall moving (u_lid, 0) on top */
+    LBM_BC_PERIODIC = 2  /* periodic in x and y                                       */
+} lbm_bc;
+
+typedef enum {
+    LBM_DRHO_CURRENT = 0, /* d rho from the density of the same step (default) */
+    LBM_DRHO_OFF = 1      /* density-gradient terms dropped                     */
+} lbm_drho;
+
+/*
+ * Run parameters.  nu is the kinematic shear viscosity; the shear relaxation
+ * rate follows Eq. transport-coefficients, nu = gamma q^2 c_s*^2
+ * (1/omega_nu - 1/2), with q = min(1, r) and c_s*^2 = 1/3 (Eqs. 1-2).
+ * omega_xi is the bulk-viscosity rate (the paper uses 1; App. A).  (fx, fy)
+ * is a uniform body force entering through the gamma-scaled sources of
+ * Eq. 13-central.  The density at the walls is rho0 = 1.
+ */
+typedef struct {
+    int32_t nx, ny;
+    double r, gamma, nu, u_lid;
+    double omega_xi;
+    double fx, fy;
+    int32_t dtype; /* lbm_dtype */
+    int32_t bc;    /* lbm_bc    */
+    int32_t drho;  /* lbm_drho  */
+    int32_t reserved;
+} lbm_params;
+
+/* Progress record filled by lbm_info. */
+typedef struct {
+    int64_t step;          /* completed time steps                              */
+    int64_t residual_step; /* step at which `residual` was evaluated (0: none)  */
+    double residual;       /* ||u_x(t) - u_x(t-20)||_2, FP64 (Sec. 5.2)         */
+    double mass;           /* sum over nodes of rho at residual_step, FP64       */
+    int32_t converged;     /* residual < tol of the last lbm_run                 */
+    int32_t diverged;      /* residual or mass non-finite                        */
+} lbm_info_t;
+
+/* Fill p with the defaults: cavity walls, omega_xi = 1, no force,
+ * LBM_DRHO_CURRENT, and the given values. EINVAL if p is NULL. */
+lbm_status lbm_params_init(lbm_params *p, int nx, int ny, double r, double gamma,
+                           double nu, double u_lid, int dtype);
+
+/* Check p without allocating: nx, ny >= 3; r > 0; 0 < gamma <= 1; nu > 0 with
+ * 0 < omega_nu < 2; 0 < omega_xi < 2; |u_lid| < q c_s*; dtype, bc, drho in
+ * range; nx * ny * 9 populations addressable. */
+lbm_status lbm_params_check(const lbm_params *p);
+
+/* Device bytes a handle needs for p (two population sets, u_x snapshot,
+ * reduction scratch, status words), for lbm_create_ex. */
+lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes);
+
+/*
+ * Create a handle with library-owned device memory (cudaMalloc on the
+ * current device) and a library-owned non-blocking stream.  The state starts
+ * at rest: every post-collision population equals w_i(r) rho0 (the rest
+ * equilibrium of Eq. 12 at u = 0).  *out is NULL on failure.
+ */
+lbm_status lbm_create(int nx, int ny, double r, double gamma, double nu, double u_lid,
+                      int dtype, lbm_t *out);
+lbm_status lbm_create_p(const lbm_params *p, lbm_t *out);
+
+/*
+ * Create a handle on caller-owned memory: `workspace` is a device buffer of
+ * at least lbm_workspace_bytes(p) bytes, 256-byte aligned, that the caller
+ * keeps alive until lbm_destroy and never frees through the library;
+ * `stream` is a cudaStream_t (NULL = legacy default stream) on which every
+ * kernel of the handle is enqueued.  ENOMEM if workspace_bytes is too small.
+ */
+lbm_status lbm_create_ex(const lbm_params *p, void *workspace, size_t workspace_bytes,
+                         void *stream, lbm_t *out);
+
+/* Switch the stream later calls enqueue on (cudaStream_t). */
+lbm_status lbm_set_stream(lbm_t h, void *stream);
+
+/* Release the handle (and its memory if library-owned). NULL is ignored. */
+void lbm_destroy(lbm_t h);
+
+/* Message of the last failing call on h (or of the last failing create when
+ * h is NULL); valid until the next call on h. */
+const char *lbm_last_error(lbm_t h);
+
+/*
+ * Enqueue n time steps (App. A, one fused kernel per step) on h's stream;
+ * asynchronous.  Every 20th step (t = 20, 40, ...) also evaluates the
+ * residual ||u_x(t) - u_x(t-20)||_2 and the total mass in FP64 (Sec. 5.2).
+ * Aligned blocks of 20 steps replay a captured CUDA graph.
+ */
+lbm_status lbm_step(lbm_t h, long n);
+
+/*
+ * Advance until the residual (evaluated every 20 steps) drops below tol, or
+ * max_steps is reached; synchronises.  *steps_done (may be NULL) receives the
+ * number of steps this call performed.  Returns OK when converged,
+ * ENOTCONVERGED when max_steps was reached first, EDIVERGED on a non-finite
+ * residual.  The device stops stepping at the step it converges (later
+ * launches of the same graph batch exit at entry).
+ */
+lbm_status lbm_run(lbm_t h, double tol, long max_steps, long *steps_done);
+
+/* Synchronise and return the last residual (FP64; +inf before step 20). */
+lbm_status lbm_residual(lbm_t h, double *res);
+
+/* Synchronise and return the total mass sum rho of the current state, FP64. */
+lbm_status lbm_mass(lbm_t h, double *mass);
+
+/* Synchronise and fill the progress record. */
+lbm_status lbm_info(lbm_t h, lbm_info_t *info);
+
+/* Wait for h's stream; reports asynchronous errors. */
+lbm_status lbm_sync(lbm_t h);
+
+/*
+ * Macroscopic fields of the current state (App. A, hydrodynamic fields):
+ * rho = sum f_i and rho u = sum f_i e_i + F / (2 gamma) of the streamed
+ * populations of the last step (computed from the stored post-collision
+ * populations as sum f~_i e_i - F / (2 gamma)).  rho, ux, uy are [ny][nx]
+ * FP64 arrays, device pointers if on_device else host; any may be NULL.
+ * Synchronises.
+ */
+lbm_status lbm_fields(lbm_t h, double *rho, double *ux, double *uy, int on_device);
+
+/*
+ * Set the state to the equilibrium of Eq. 12 (no corrections) of the given
+ * fields: f~_i = f^eq_i(rho, u) at every node.  Arrays [ny][nx] FP64, device
+ * pointers if on_device else host.  Resets the step counter to 0 and the
+ * residual snapshot to this u_x.
+ */
+lbm_status lbm_init_fields(lbm_t h, const double *rho, const double *ux, const double *uy,
+                           int on_device);
+
+/*
+ * Set / get the post-collision populations f~_i, [9][ny][nx] FP64 (device
+ * pointer if on_device else host).  Set rounds to the storage precision
+ * (round-to-nearest-even) and resets the step counter and the snapshot.
+ */
+lbm_status lbm_set_populations(lbm_t h, const double *f, int on_device);
+lbm_status lbm_get_populations(lbm_t h, double *f, int on_device);
+
+/*
+ * Checkpoint: copy the raw storage (populations, snapshot, step counter,
+ * last residual) to a host buffer of lbm_save_bytes(h) bytes; lbm_load
+ * restores it bitwise, so a resumed run equals an uninterrupted one.
+ */
+lbm_status lbm_save_bytes(lbm_t h, size_t *bytes);
+lbm_status lbm_save(lbm_t h, void *host_buf, size_t n);
+lbm_status lbm_load(lbm_t h, const void *host_buf, size_t n);
+
+/* Derived constants: shear relaxation rate omega_nu and q = min(1, r). */
+lbm_status lbm_omega_nu(const lbm_params *p, double *omega_nu);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRC_LBM_H */

@@ -1,0 +1,812 @@
+// lbm_api.cu -- the C ABI of include/prc_lbm.h: handles, workspace layout,
+// per-instance constants, step scheduling (CUDA graphs of 20 steps), the
+// device-side stop rule of lbm_run, residual/mass finalisation, field and
+// population transfers, checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "prc_lbm.h"
+#include "prc_ops.h"
+
+using prc::Coef;
+using prc::DevStatus;
+using prc::Grid;
+
+namespace {
+
+constexpr int RES_INTERVAL = 20;  // residual every 20 steps (Sec. 5.2)
+constexpr size_t ALIGN = 256;
+
+thread_local std::string g_err;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+const prc::DtypeOps *ops_for(int dtype)
+{
+    switch (dtype) {
+    case LBM_F64: return &prc::ops_f64;
+    case LBM_F32: return &prc::ops_f32;
+    case LBM_F16: return &prc::ops_f16;
+    default: return nullptr;
+    }
+}
+
+struct Layout {
+    int pitch;
+    size_t plane, pop_bytes, snap_bytes, part_bytes, st_bytes;
+    size_t off_pop0, off_pop1, off_snap, off_part, off_st, total;
+    int nparts;
+};
+
+Layout make_layout(const lbm_params &p)
+{
+    const prc::DtypeOps *ops = ops_for(p.dtype);
+    Layout L;
+    L.pitch = (int)align_up((size_t)p.nx, 32);
+    L.plane = (size_t)L.pitch * (size_t)p.ny;
+    L.pop_bytes = align_up(9 * L.plane * ops->elem, ALIGN);
+    L.snap_bytes = align_up(L.plane * ops->snap_elem, ALIGN);
+    L.nparts = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    L.part_bytes = align_up((size_t)L.nparts * sizeof(double2), ALIGN);
+    L.st_bytes = align_up(sizeof(DevStatus), ALIGN);
+    L.off_pop0 = 0;
+    L.off_pop1 = L.off_pop0 + L.pop_bytes;
+    L.off_snap = L.off_pop1 + L.pop_bytes;
+    L.off_part = L.off_snap + L.snap_bytes;
+    L.off_st = L.off_part + L.part_bytes;
+    L.total = L.off_st + L.st_bytes;
+    return L;
+}
+
+double q_of(double r) { return r < 1.0 ? r : 1.0; }
+
+double omega_nu_of(const lbm_params &p)
+{
+    const double c2 = q_of(p.r) * q_of(p.r) / 3.0;
+    return 1.0 / (p.nu / (p.gamma * c2) + 0.5);
+}
+
+// Per-instance constants (App. A coefficients with dt = 1).
+void make_coef(const lbm_params &p, Coef<double> &k)
+{
+    std::memset(&k, 0, sizeof(k));
+    const double r = p.r, q = q_of(r), c2 = q * q / 3.0, g = p.gamma;
+    const double w_nu = omega_nu_of(p), w_xi = p.omega_xi;
+    const double tau_nu = 1.0 / w_nu - 0.5, tau_xi = 1.0 / w_xi - 0.5;
+    const double Pg = 4.0 / (g * g) - 1.0 / g, Qg = 1.0 / (g * g) - 1.0 / g, Ug = 2.0 / g + 1.0;
+    k.r = r;
+    k.r2 = r * r;
+    k.inv_r = 1.0 / r;
+    k.inv_r2 = 1.0 / (r * r);
+    k.c2 = c2;
+    k.c4 = c2 * c2;
+    k.w_nu = w_nu;
+    k.w_xi = w_xi;
+    k.one_m_w_nu = 1.0 - w_nu;
+    k.one_m_w_xi = 1.0 - w_xi;
+    k.src_nu = 1.0 - 0.5 * w_nu;
+    k.src_xi = 1.0 - 0.5 * w_xi;
+    k.m2tau_nu = -2.0 * tau_nu;
+    k.m2tau_xi = -2.0 * tau_xi;
+    k.mtau_nu = -tau_nu;
+    k.ig = 1.0 / g;
+    k.h1 = 1.0 / g - 1.0;
+    k.a3 = 1.0 / (g * g) - 3.0 / g + 2.0;
+    k.Pg = Pg;
+    k.Qg = Qg;
+    k.hPg = 0.5 * Pg;
+    k.hQg = 0.5 * Qg;
+    k.Ax = 0.5 * (Ug * c2 - 1.0);
+    k.By = 0.5 * (Ug * c2 - r * r);
+    k.k3x = 0.5 * (3.0 * c2 - 1.0);
+    k.k3y = 0.5 * (3.0 * c2 - r * r);
+    k.Cb0 = -2.0 * c2 / w_xi;
+    k.Cs0 = -2.0 * c2 / w_nu;
+    k.h1c2 = (1.0 / g - 1.0) * c2;
+    k.hx = p.fx / (2.0 * g);
+    k.hy = p.fy / (2.0 * g);
+    k.twoQFx = 2.0 * Qg * p.fx;
+    k.twoQFy = 2.0 * Qg * p.fy;
+    k.QFx = Qg * p.fx;
+    k.QFy = Qg * p.fy;
+    const bool lid_on = (p.bc != LBM_BC_PERIODIC) && (p.u_lid != 0.0);
+    k.lid = lid_on ? c2 * p.u_lid / (2.0 * r * r) : 0.0;
+    k.inv12 = 1.0 / 12.0;
+    k.inv12r = 1.0 / (12.0 * r);
+    // rest populations: the unique f with the rest moments (1, 0, 0, c^2,
+    // c^2, 0, 0, 0, c^4) of Eq. 12 at u = 0, through S^-1 and P^-1
+    const double a = c2, b = c2 / (r * r), cc = c2 * c2 / (r * r);
+    k.w[0] = 1.0 - a - b + cc;
+    k.w[1] = k.w[3] = 0.5 * (a - cc);
+    k.w[2] = k.w[4] = 0.5 * (b - cc);
+    k.w[5] = k.w[6] = k.w[7] = k.w[8] = 0.25 * cc;
+}
+
+Grid make_grid(const lbm_params &p, const Layout &L)
+{
+    Grid gd;
+    gd.nx = p.nx;
+    gd.ny = p.ny;
+    gd.pitch = L.pitch;
+    gd.bc = p.bc;
+    gd.plane = (long long)L.plane;
+    gd.lid_on = (p.bc != LBM_BC_PERIODIC) && (p.u_lid != 0.0);
+    gd.pad = 0;
+    return gd;
+}
+
+// Fixed-order two-level reduction of the per-CTA partials (deterministic).
+__device__ void reduce_partials(const double2 *partials, int n, double &a, double &b)
+{
+    __shared__ double sa[256], sb[256];
+    const int t = threadIdx.x;
+    double x = 0.0, y = 0.0;
+    for (int i = t; i < n; i += 256) {
+        x += partials[i].x;
+        y += partials[i].y;
+    }
+    sa[t] = x;
+    sb[t] = y;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sa[t] += sa[t + s];
+            sb[t] += sb[t + s];
+        }
+        __syncthreads();
+    }
+    a = sa[0];
+    b = sb[0];
+}
+
+// Residual and mass of a residual step; the stop rule of lbm_run.
+__global__ void __launch_bounds__(256) k_finalize(const double2 *partials, int n, DevStatus *st, double nnodes)
+{
+    if (st->stop) return;
+    double a, b;
+    reduce_partials(partials, n, a, b);
+    if (threadIdx.x == 0) {
+        const double res = sqrt(a), mass = nnodes + b;
+        st->res_step += RES_INTERVAL;
+        st->res = res;
+        st->mass = mass;
+        if (!isfinite(res) || !isfinite(mass)) {
+            st->diverged = 1;
+            st->stop = 1;
+        } else if (res < st->tol) {
+            st->converged = 1;
+            st->stop = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mass_final(const double2 *partials, int n, DevStatus *st, double nnodes)
+{
+    double a, b;
+    reduce_partials(partials, n, a, b);
+    if (threadIdx.x == 0) st->mass_now = nnodes + b;
+}
+
+__global__ void k_status_reset(DevStatus *st)
+{
+    st->stop = 0;
+    st->converged = 0;
+    st->diverged = 0;
+    st->timeout = 0;
+    st->res_step = 0;
+    st->tol = -1.0;
+    st->res = INFINITY;
+    st->mass = 0.0;
+    st->mass_now = 0.0;
+}
+
+__global__ void k_status_arm(DevStatus *st, double tol)
+{
+    st->tol = tol;
+    st->converged = 0;
+    st->stop = st->diverged ? 1 : 0;
+}
+
+}  // namespace
+
+struct lbm_s {
+    lbm_params p;
+    const prc::DtypeOps *ops;
+    Layout L;
+    Grid gd;
+    Coef<double> k;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    char *ws;
+    bool own_ws;
+    void *pop[2];
+    void *snap;
+    double2 *partials;
+    DevStatus *st;
+    DevStatus *st_host;  // pinned mirror
+    long long t;         // completed steps; invariant: the state is in pop[t & 1]
+    cudaGraphExec_t g20;
+    bool have_g20;
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_t h, lbm_status s, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_err = msg;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_t h, cudaError_t e, const char *what)
+{
+    return fail(h, LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                          \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+lbm_status enter(lbm_t h)
+{
+    if (!h) return fail(nullptr, LBM_EINVAL, "null handle");
+    h->err.clear();
+    CK(h, cudaSetDevice(h->device));
+    return LBM_OK;
+}
+
+void *cur_pop(lbm_t h) { return h->pop[h->t & 1]; }
+
+// one step; the state moves from pop[t&1] to pop[(t+1)&1]
+lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
+{
+    const bool epi = ((t_before + 1) % RES_INTERVAL) == 0;
+    const int c = (int)(t_before & 1);
+    CK(h, h->ops->step(h->pop[c], h->pop[c ^ 1], h->gd, h->k, h->snap, h->partials, h->st,
+                       h->p.drho == LBM_DRHO_CURRENT, epi, s));
+    if (epi) {
+        k_finalize<<<1, 256, 0, s>>>(h->partials, h->L.nparts, h->st, (double)h->p.nx * (double)h->p.ny);
+        CK(h, cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+// CUDA graph of the 20 steps t = 20m .. 20m+19 (state starts and ends in pop[0]).
+lbm_status ensure_graph(lbm_t h)
+{
+    if (h->have_g20) return LBM_OK;
+    cudaStream_t cs;
+    CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(h, e, "cudaStreamBeginCapture");
+    }
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < RES_INTERVAL && st == LBM_OK; i++) st = launch_one(h, cs, i);
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st != LBM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->g20, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    h->have_g20 = true;
+    return LBM_OK;
+}
+
+lbm_status enqueue_steps(lbm_t h, long long n)
+{
+    while (n > 0) {
+        if ((h->t % RES_INTERVAL) == 0 && n >= RES_INTERVAL) {
+            lbm_status s = ensure_graph(h);
+            if (s != LBM_OK) return s;
+            CK(h, cudaGraphLaunch(h->g20, h->stream));
+            h->t += RES_INTERVAL;
+            n -= RES_INTERVAL;
+        } else {
+            lbm_status s = launch_one(h, h->stream, h->t);
+            if (s != LBM_OK) return s;
+            h->t += 1;
+            n -= 1;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status read_status(lbm_t h)
+{
+    CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status reset_state_meta(lbm_t h)
+{
+    h->t = 0;
+    k_status_reset<<<1, 1, 0, h->stream>>>(h->st);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+// device scratch for host<->device transfers of fields / populations
+struct DevTmp {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevTmp()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+lbm_status init_handle(lbm_t h, const lbm_params &p, void *ws, size_t ws_bytes, bool own_ws, cudaStream_t stream,
+                       bool own_stream)
+{
+    h->p = p;
+    h->ops = ops_for(p.dtype);
+    h->L = make_layout(p);
+    h->gd = make_grid(p, h->L);
+    make_coef(p, h->k);
+    h->stream = stream;
+    h->own_stream = own_stream;
+    h->ws = static_cast<char *>(ws);
+    h->own_ws = own_ws;
+    (void)ws_bytes;
+    h->pop[0] = h->ws + h->L.off_pop0;
+    h->pop[1] = h->ws + h->L.off_pop1;
+    h->snap = h->ws + h->L.off_snap;
+    h->partials = reinterpret_cast<double2 *>(h->ws + h->L.off_part);
+    h->st = reinterpret_cast<DevStatus *>(h->ws + h->L.off_st);
+    h->t = 0;
+    h->have_g20 = false;
+    CK(h, cudaMallocHost(&h->st_host, sizeof(DevStatus)));
+    // rest state f~ = w(r): zero shifted storage everywhere (padding too)
+    CK(h, cudaMemsetAsync(h->ws, 0, h->L.off_part, h->stream));
+    return reset_state_meta(h);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// public entry points
+
+extern "C" {
+
+lbm_status lbm_params_init(lbm_params *p, int nx, int ny, double r, double gamma, double nu, double u_lid,
+                           int dtype)
+{
+    if (!p) return fail(nullptr, LBM_EINVAL, "null params");
+    std::memset(p, 0, sizeof(*p));
+    p->nx = nx;
+    p->ny = ny;
+    p->r = r;
+    p->gamma = gamma;
+    p->nu = nu;
+    p->u_lid = u_lid;
+    p->omega_xi = 1.0;
+    p->dtype = dtype;
+    p->bc = LBM_BC_CAVITY;
+    p->drho = LBM_DRHO_CURRENT;
+    return LBM_OK;
+}
+
+lbm_status lbm_params_check(const lbm_params *p)
+{
+    if (!p) return fail(nullptr, LBM_EINVAL, "null params");
+    if (p->nx < 3 || p->ny < 3) return fail(nullptr, LBM_EINVAL, "nx and ny must be >= 3");
+    if (p->nx > (1 << 28) || p->ny > (1 << 28) || (double)p->nx * (double)p->ny > 4.0e10)
+        return fail(nullptr, LBM_EINVAL, "grid too large");
+    if (!(p->r > 0.0) || !std::isfinite(p->r)) return fail(nullptr, LBM_EINVAL, "r must be > 0");
+    if (!(p->gamma > 0.0 && p->gamma <= 1.0)) return fail(nullptr, LBM_EINVAL, "gamma must be in (0, 1]");
+    if (!(p->nu > 0.0) || !std::isfinite(p->nu)) return fail(nullptr, LBM_EINVAL, "nu must be > 0");
+    const double w = omega_nu_of(*p);
+    if (!(w > 0.0 && w < 2.0)) return fail(nullptr, LBM_EINVAL, "omega_nu outside (0, 2)");
+    if (!(p->omega_xi > 0.0 && p->omega_xi < 2.0)) return fail(nullptr, LBM_EINVAL, "omega_xi outside (0, 2)");
+    if (!std::isfinite(p->u_lid) || std::fabs(p->u_lid) >= q_of(p->r) / std::sqrt(3.0))
+        return fail(nullptr, LBM_EINVAL, "|u_lid| must be below the sound speed q c_s*");
+    if (!std::isfinite(p->fx) || !std::isfinite(p->fy)) return fail(nullptr, LBM_EINVAL, "force not finite");
+    if (!ops_for(p->dtype)) return fail(nullptr, LBM_EINVAL, "unknown dtype");
+    if (p->bc < LBM_BC_CAVITY || p->bc > LBM_BC_PERIODIC) return fail(nullptr, LBM_EINVAL, "unknown bc");
+    if (p->drho != LBM_DRHO_CURRENT && p->drho != LBM_DRHO_OFF) return fail(nullptr, LBM_EINVAL, "unknown drho");
+    return LBM_OK;
+}
+
+lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes)
+{
+    lbm_status s = lbm_params_check(p);
+    if (s != LBM_OK) return s;
+    if (!bytes) return fail(nullptr, LBM_EINVAL, "null bytes");
+    *bytes = make_layout(*p).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_omega_nu(const lbm_params *p, double *omega_nu)
+{
+    lbm_status s = lbm_params_check(p);
+    if (s != LBM_OK) return s;
+    if (!omega_nu) return fail(nullptr, LBM_EINVAL, "null out");
+    *omega_nu = omega_nu_of(*p);
+    return LBM_OK;
+}
+
+lbm_status lbm_create_p(const lbm_params *p, lbm_t *out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "null out");
+    *out = nullptr;
+    lbm_status s = lbm_params_check(p);
+    if (s != LBM_OK) return s;
+    lbm_t h = new (std::nothrow) lbm_s();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    const size_t bytes = make_layout(*p).total;
+    void *ws = nullptr;
+    e = cudaMalloc(&ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, LBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    cudaStream_t stream;
+    e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(ws);
+        delete h;
+        return fail(nullptr, LBM_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    s = init_handle(h, *p, ws, bytes, true, stream, true);
+    if (s != LBM_OK) {
+        g_err = h->err;
+        lbm_destroy(h);
+        return s;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(int nx, int ny, double r, double gamma, double nu, double u_lid, int dtype, lbm_t *out)
+{
+    lbm_params p;
+    lbm_params_init(&p, nx, ny, r, gamma, nu, u_lid, dtype);
+    return lbm_create_p(&p, out);
+}
+
+lbm_status lbm_create_ex(const lbm_params *p, void *workspace, size_t workspace_bytes, void *stream, lbm_t *out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "null out");
+    *out = nullptr;
+    lbm_status s = lbm_params_check(p);
+    if (s != LBM_OK) return s;
+    if (!workspace) return fail(nullptr, LBM_EINVAL, "null workspace");
+    if (reinterpret_cast<uintptr_t>(workspace) % ALIGN) return fail(nullptr, LBM_EINVAL, "workspace not 256-byte aligned");
+    if (workspace_bytes < make_layout(*p).total) return fail(nullptr, LBM_ENOMEM, "workspace too small");
+    lbm_t h = new (std::nothrow) lbm_s();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    s = init_handle(h, *p, workspace, workspace_bytes, false, static_cast<cudaStream_t>(stream), false);
+    if (s != LBM_OK) {
+        g_err = h->err;
+        lbm_destroy(h);
+        return s;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_t h, void *stream)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->own_stream) CK(h, cudaStreamDestroy(h->stream));
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->own_stream = false;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_t h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->have_g20) cudaGraphExecDestroy(h->g20);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char *lbm_last_error(lbm_t h)
+{
+    return h ? h->err.c_str() : g_err.c_str();
+}
+
+lbm_status lbm_step(lbm_t h, long n)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (n < 0) return fail(h, LBM_EINVAL, "negative step count");
+    k_status_arm<<<1, 1, 0, h->stream>>>(h->st, -1.0);
+    CK(h, cudaGetLastError());
+    return enqueue_steps(h, n);
+}
+
+lbm_status lbm_run(lbm_t h, double tol, long max_steps, long *steps_done)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (max_steps < 0 || !(tol == tol)) return fail(h, LBM_EINVAL, "bad tol / max_steps");
+    const long long t0 = h->t;
+    long long left = max_steps;
+    k_status_arm<<<1, 1, 0, h->stream>>>(h->st, tol);
+    CK(h, cudaGetLastError());
+    // align to a residual boundary with single launches
+    while (left > 0 && (h->t % RES_INTERVAL) != 0) {
+        s = launch_one(h, h->stream, h->t);
+        if (s != LBM_OK) return s;
+        h->t++;
+        left--;
+        if ((h->t % RES_INTERVAL) == 0) {
+            s = read_status(h);
+            if (s != LBM_OK) return s;
+            if (h->st_host->stop) break;
+        }
+    }
+    long long batch = 8;  // graph replays per host check
+    s = read_status(h);
+    if (s != LBM_OK) return s;
+    while (!h->st_host->stop && left >= RES_INTERVAL) {
+        s = ensure_graph(h);
+        if (s != LBM_OK) return s;
+        long long nb = left / RES_INTERVAL;
+        if (nb > batch) nb = batch;
+        for (long long i = 0; i < nb; i++) CK(h, cudaGraphLaunch(h->g20, h->stream));
+        s = read_status(h);
+        if (s != LBM_OK) return s;
+        if (h->st_host->stop) {
+            const long long done = h->st_host->res_step - h->t;  // steps actually performed
+            h->t = h->st_host->res_step;
+            left -= done;
+            break;
+        }
+        h->t += nb * RES_INTERVAL;
+        left -= nb * RES_INTERVAL;
+        if (batch < 2048) batch *= 2;
+    }
+    if (!h->st_host->stop && left > 0) {  // tail shorter than one residual block
+        s = enqueue_steps(h, left);
+        if (s != LBM_OK) return s;
+        s = read_status(h);
+        if (s != LBM_OK) return s;
+    }
+    if (steps_done) *steps_done = (long)(h->t - t0);
+    if (h->st_host->diverged) return fail(h, LBM_EDIVERGED, "residual or mass not finite");
+    if (h->st_host->converged) return LBM_OK;
+    return LBM_ENOTCONVERGED;
+}
+
+lbm_status lbm_sync(lbm_t h)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_info(lbm_t h, lbm_info_t *info)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!info) return fail(h, LBM_EINVAL, "null info");
+    s = read_status(h);
+    if (s != LBM_OK) return s;
+    info->step = h->t;
+    info->residual_step = h->st_host->res_step;
+    info->residual = h->st_host->res_step > 0 ? h->st_host->res : INFINITY;
+    info->mass = h->st_host->mass;
+    info->converged = h->st_host->converged;
+    info->diverged = h->st_host->diverged;
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_t h, double *res)
+{
+    if (!res) return fail(h, LBM_EINVAL, "null out");
+    lbm_info_t info;
+    lbm_status s = lbm_info(h, &info);
+    if (s != LBM_OK) return s;
+    *res = info.residual;
+    return info.diverged ? LBM_EDIVERGED : LBM_OK;
+}
+
+lbm_status lbm_mass(lbm_t h, double *mass)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!mass) return fail(h, LBM_EINVAL, "null out");
+    CK(h, h->ops->mass_partial(cur_pop(h), h->gd, h->partials, h->stream));
+    k_mass_final<<<1, 256, 0, h->stream>>>(h->partials, h->L.nparts, h->st, (double)h->p.nx * (double)h->p.ny);
+    CK(h, cudaGetLastError());
+    s = read_status(h);
+    if (s != LBM_OK) return s;
+    *mass = h->st_host->mass_now;
+    return std::isfinite(*mass) ? LBM_OK : LBM_EDIVERGED;
+}
+
+lbm_status lbm_fields(lbm_t h, double *rho, double *ux, double *uy, int on_device)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    if (on_device) {
+        CK(h, h->ops->fields(cur_pop(h), h->gd, h->k, rho, ux, uy, nullptr, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    DevTmp tmp;
+    tmp.s = h->stream;
+    CK(h, cudaMallocAsync(&tmp.p, 3 * n * sizeof(double), h->stream));
+    double *d = static_cast<double *>(tmp.p);
+    CK(h, h->ops->fields(cur_pop(h), h->gd, h->k, d, d + n, d + 2 * n, nullptr, h->stream));
+    double *outs[3] = {rho, ux, uy};
+    for (int i = 0; i < 3; i++)
+        if (outs[i]) CK(h, cudaMemcpyAsync(outs[i], d + i * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_t h, const double *rho, const double *ux, const double *uy, int on_device)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!rho || !ux || !uy) return fail(h, LBM_EINVAL, "null field");
+    const size_t n = (size_t)h->p.nx * h->p.ny;
+    DevTmp tmp;
+    tmp.s = h->stream;
+    const double *d[3] = {rho, ux, uy};
+    if (!on_device) {
+        CK(h, cudaMallocAsync(&tmp.p, 3 * n * sizeof(double), h->stream));
+        double *b = static_cast<double *>(tmp.p);
+        for (int i = 0; i < 3; i++) {
+            CK(h, cudaMemcpyAsync(b + i * n, d[i], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            d[i] = b + i * n;
+        }
+    }
+    s = reset_state_meta(h);
+    if (s != LBM_OK) return s;
+    CK(h, h->ops->init_fields(h->pop[0], h->gd, h->k, h->p.gamma, d[0], d[1], d[2], h->snap, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_t h, const double *f, int on_device)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(h, LBM_EINVAL, "null populations");
+    const size_t n = 9 * (size_t)h->p.nx * h->p.ny;
+    DevTmp tmp;
+    tmp.s = h->stream;
+    const double *d = f;
+    if (!on_device) {
+        CK(h, cudaMallocAsync(&tmp.p, n * sizeof(double), h->stream));
+        CK(h, cudaMemcpyAsync(tmp.p, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        d = static_cast<const double *>(tmp.p);
+    }
+    s = reset_state_meta(h);
+    if (s != LBM_OK) return s;
+    CK(h, h->ops->set_pop(h->pop[0], h->gd, h->k, d, h->stream));
+    CK(h, h->ops->fields(h->pop[0], h->gd, h->k, nullptr, nullptr, nullptr, h->snap, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_t h, double *f, int on_device)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(h, LBM_EINVAL, "null populations");
+    const size_t n = 9 * (size_t)h->p.nx * h->p.ny;
+    if (on_device) {
+        CK(h, h->ops->get_pop(cur_pop(h), h->gd, h->k, f, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return LBM_OK;
+    }
+    DevTmp tmp;
+    tmp.s = h->stream;
+    CK(h, cudaMallocAsync(&tmp.p, n * sizeof(double), h->stream));
+    CK(h, h->ops->get_pop(cur_pop(h), h->gd, h->k, static_cast<double *>(tmp.p), h->stream));
+    CK(h, cudaMemcpyAsync(f, tmp.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+namespace {
+struct SaveHeader {
+    char magic[8];
+    int32_t version, nx, ny, dtype;
+    int64_t t;
+    DevStatus st;
+    uint64_t pop_bytes, snap_bytes;
+};
+}  // namespace
+
+lbm_status lbm_save_bytes(lbm_t h, size_t *bytes)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!bytes) return fail(h, LBM_EINVAL, "null out");
+    *bytes = sizeof(SaveHeader) + h->L.pop_bytes + h->L.snap_bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_save(lbm_t h, void *host_buf, size_t n)
+{
+    size_t need = 0;
+    lbm_status s = lbm_save_bytes(h, &need);
+    if (s != LBM_OK) return s;
+    if (!host_buf || n < need) return fail(h, LBM_EINVAL, "checkpoint buffer too small");
+    s = read_status(h);
+    if (s != LBM_OK) return s;
+    SaveHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "PRCLBM1", 8);
+    hd.version = 1;
+    hd.nx = h->p.nx;
+    hd.ny = h->p.ny;
+    hd.dtype = h->p.dtype;
+    hd.t = h->t;
+    hd.st = *h->st_host;
+    hd.pop_bytes = h->L.pop_bytes;
+    hd.snap_bytes = h->L.snap_bytes;
+    char *b = static_cast<char *>(host_buf);
+    std::memcpy(b, &hd, sizeof(hd));
+    CK(h, cudaMemcpyAsync(b + sizeof(hd), cur_pop(h), h->L.pop_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(b + sizeof(hd) + h->L.pop_bytes, h->snap, h->L.snap_bytes, cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_t h, const void *host_buf, size_t n)
+{
+    size_t need = 0;
+    lbm_status s = lbm_save_bytes(h, &need);
+    if (s != LBM_OK) return s;
+    if (!host_buf || n < need) return fail(h, LBM_EINVAL, "checkpoint buffer too small");
+    SaveHeader hd;
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "PRCLBM1", 8) != 0 || hd.version != 1 || hd.nx != h->p.nx || hd.ny != h->p.ny ||
+        hd.dtype != h->p.dtype || hd.pop_bytes != h->L.pop_bytes || hd.snap_bytes != h->L.snap_bytes)
+        return fail(h, LBM_EINVAL, "checkpoint does not match this handle");
+    const char *b = static_cast<const char *>(host_buf);
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->t = hd.t;
+    CK(h, cudaMemcpyAsync(cur_pop(h), b + sizeof(hd), h->L.pop_bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->snap, b + sizeof(hd) + h->L.pop_bytes, h->L.snap_bytes, cudaMemcpyHostToDevice,
+                          h->stream));
+    *h->st_host = hd.st;
+    CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

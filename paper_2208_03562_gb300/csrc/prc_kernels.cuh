@@ -1,0 +1,208 @@
+// prc_kernels.cuh -- kernels of the single-instance path, templated on the
+// storage type S (double, float, __half) and the collision type T.
+#pragma once
+
+#include "prc_device.cuh"
+
+namespace prc {
+
+constexpr int BX = 32;  // tile width  (nodes, one per thread)
+constexpr int BY = 8;   // tile height
+constexpr int NRING = 2 * (BX + 2) + 2 * BY;
+
+// Warp-shuffle then CTA reduction of two FP64 sums; thread 0 gets the totals.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *sm /* 2 * nwarps */)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    if ((tid & 31) == 0) {
+        sm[tid >> 5] = a;
+        sm[nw + (tid >> 5)] = b;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        a = tid < nw ? sm[tid] : 0.0;
+        b = tid < nw ? sm[nw + tid] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+// One fused time step: pull-stream + walls, density tile (+1 ring) in shared
+// memory for the density gradient, collision, store.  With EPI the step also
+// evaluates (u_x - u_x,snapshot)^2 and drho per CTA in FP64 for the residual
+// of Sec. 5.2 and refreshes the snapshot.
+template <typename S, typename T, bool DRHO, bool EPI>
+__global__ void __launch_bounds__(BX * BY)
+k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
+       double2 *__restrict__ partials, const DevStatus *__restrict__ st)
+{
+    if (st->stop) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool valid = (x < gd.nx) & (y < gd.ny);
+
+    T g[9];
+    int mx = x, my = y;
+    map_node(gd, mx, my);
+    pull9<S, T>(src, gd, mx, my, k.lid, g);
+
+    T dxr = T(0), dyr = T(0);
+    if constexpr (DRHO) {
+        __shared__ T srho[BY + 2][BX + 2];
+        srho[ty + 1][tx + 1] = sum9(g);
+        const int tid = ty * BX + tx;
+        if (tid < NRING) {
+            int lx, ly;
+            if (tid < BX + 2) { lx = tid; ly = 0; }
+            else if (tid < 2 * (BX + 2)) { lx = tid - (BX + 2); ly = BY + 1; }
+            else if (tid < 2 * (BX + 2) + BY) { lx = 0; ly = tid - 2 * (BX + 2) + 1; }
+            else { lx = BX + 1; ly = tid - 2 * (BX + 2) - BY + 1; }
+            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            map_node(gd, gx, gy);
+            T gr[9];
+            pull9<S, T>(src, gd, gx, gy, k.lid, gr);
+            srho[ly][lx] = sum9(gr);
+        }
+        __syncthreads();
+        const int cx = tx + 1, cy = ty + 1;
+        const T rE = srho[cy][cx + 1], rW = srho[cy][cx - 1];
+        const T rN = srho[cy + 1][cx], rS = srho[cy - 1][cx];
+        const T rNE = srho[cy + 1][cx + 1], rNW = srho[cy + 1][cx - 1];
+        const T rSE = srho[cy - 1][cx + 1], rSW = srho[cy - 1][cx - 1];
+        dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
+        dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+    }
+
+    T ux = T(0), uy = T(0), drho = T(0);
+    if (valid) {
+        collide<T, DRHO>(k, g, dxr, dyr, ux, uy, drho);
+        const long long o = (long long)y * gd.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>(g[i]);
+    }
+    if constexpr (EPI) {
+        __shared__ double sm[2 * (BX * BY / 32)];
+        double d2 = 0.0, dm = 0.0;
+        if (valid) {
+            const long long o = (long long)y * gd.pitch + x;
+            const double d = (double)ux - (double)snap[o];
+            snap[o] = ux;
+            d2 = d * d;
+            dm = (double)drho;
+        }
+        block_sum2(d2, dm, sm);
+        if (ty == 0 && tx == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(d2, dm);
+    }
+}
+
+// f~ = f^eq(rho, u) (Eq. 12, uncorrected), stored shifted; snapshot = u_x.
+template <typename S, typename T>
+__global__ void k_init_fields(S *__restrict__ dst, Grid gd, Coef<double> k, double gamma,
+                              const double *__restrict__ rho_in, const double *__restrict__ ux_in,
+                              const double *__restrict__ uy_in, T *__restrict__ snap)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= gd.nx || y >= gd.ny) return;
+    const long long n = (long long)y * gd.nx + x;
+    const double rho = rho_in[n], ux = ux_in[n], uy = uy_in[n];
+    const double drho = rho - 1.0, ig = 1.0 / gamma;
+    // raw equilibrium moments (rectangular) minus the rest-state moments
+    const double D00 = drho, D10 = rho * ux, D01 = rho * uy;
+    const double D20 = k.c2 * drho + rho * ux * ux * ig;
+    const double D02 = k.c2 * drho + rho * uy * uy * ig;
+    const double D11 = rho * ux * uy * ig;
+    const double D21 = rho * (k.c2 + ux * ux * ig * ig) * uy;
+    const double D12 = rho * (k.c2 + uy * uy * ig * ig) * ux;
+    const double D22 = k.c4 * drho + rho * k.c2 * (ux * ux + uy * uy) + rho * ux * ux * uy * uy;
+    const double e01 = D01 * k.inv_r, e02 = D02 * k.inv_r2, e11 = D11 * k.inv_r;
+    const double e21 = D21 * k.inv_r, e12 = D12 * k.inv_r2, e22 = D22 * k.inv_r2;
+    double g[9];
+    g[0] = D00 - D20 - e02 + e22;
+    g[1] = 0.5 * (D10 + D20 - e12 - e22);
+    g[2] = 0.5 * (e01 + e02 - e21 - e22);
+    g[3] = 0.5 * (-D10 + D20 + e12 - e22);
+    g[4] = 0.5 * (-e01 + e02 + e21 - e22);
+    g[5] = 0.25 * (e11 + e21 + e12 + e22);
+    g[6] = 0.25 * (-e11 + e21 - e12 + e22);
+    g[7] = 0.25 * (e11 - e21 - e12 + e22);
+    g[8] = 0.25 * (-e11 - e21 + e12 + e22);
+    const long long o = (long long)y * gd.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>((T)g[i]);
+    snap[o] = (T)ux;
+}
+
+// Fields of the stored post-collision state: rho = 1 + sum g, rho u = sum g e
+// - F / (2 gamma) (the rest state carries no momentum).
+template <typename S, typename T>
+__global__ void k_fields(const S *__restrict__ src, Grid gd, Coef<double> k, double *__restrict__ rho_out,
+                         double *__restrict__ ux_out, double *__restrict__ uy_out, T *__restrict__ snap)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= gd.nx || y >= gd.ny) return;
+    const long long o = (long long)y * gd.pitch + x;
+    double g[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) g[i] = (double)ld_s<S, T>(src + (long long)i * gd.plane + o);
+    const double s00 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const double s10 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const double s01 = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    const double rho = 1.0 + s00;
+    const double ux = (s10 - k.hx) / rho, uy = (k.r * s01 - k.hy) / rho;
+    const long long n = (long long)y * gd.nx + x;
+    if (rho_out) rho_out[n] = rho;
+    if (ux_out) ux_out[n] = ux;
+    if (uy_out) uy_out[n] = uy;
+    if (snap) snap[o] = (T)ux;
+}
+
+// Full FP64 populations <-> shifted storage.
+template <typename S, typename T>
+__global__ void k_set_pop(S *__restrict__ dst, Grid gd, Coef<double> k, const double *__restrict__ f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= gd.nx || y >= gd.ny) return;
+    const long long nn = (long long)gd.nx * gd.ny, n = (long long)y * gd.nx + x;
+    const long long o = (long long)y * gd.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>((T)(f[i * nn + n] - k.w[i]));
+}
+
+template <typename S, typename T>
+__global__ void k_get_pop(const S *__restrict__ src, Grid gd, Coef<double> k, double *__restrict__ f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= gd.nx || y >= gd.ny) return;
+    const long long nn = (long long)gd.nx * gd.ny, n = (long long)y * gd.nx + x;
+    const long long o = (long long)y * gd.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i * nn + n] = (double)ld_s<S, T>(src + (long long)i * gd.plane + o) + k.w[i];
+}
+
+// Per-CTA FP64 partial sums of sum_i g_i (total mass minus the node count).
+template <typename S, typename T>
+__global__ void __launch_bounds__(BX * BY) k_mass_partial(const S *__restrict__ src, Grid gd, double2 *__restrict__ partials)
+{
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+    double dm = 0.0, z = 0.0;
+    if (x < gd.nx && y < gd.ny) {
+        const long long o = (long long)y * gd.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; i++) dm += (double)ld_s<S, T>(src + (long long)i * gd.plane + o);
+    }
+    __shared__ double sm[2 * (BX * BY / 32)];
+    block_sum2(z, dm, sm);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(z, dm);
+}
+
+}  // namespace prc

@@ -1,0 +1,40 @@
+// prc_ops.h -- internal interface between the C ABI (lbm_api.cu) and the
+// per-storage-type kernel translation units (ops_f64.cu, ops_f32.cu,
+// ops_f16.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "prc_device.cuh"
+
+namespace prc {
+
+template <typename T>
+inline Coef<T> cast_coef(const Coef<double> &d)
+{
+    Coef<T> c;
+    const double *s = reinterpret_cast<const double *>(&d);
+    T *o = reinterpret_cast<T *>(&c);
+    for (size_t i = 0; i < sizeof(Coef<double>) / sizeof(double); i++) o[i] = (T)s[i];
+    return c;
+}
+
+struct DtypeOps {
+    size_t elem;       // bytes per stored population
+    size_t snap_elem;  // bytes per snapshot value (collision precision)
+    cudaError_t (*step)(const void *src, void *dst, const Grid &gd, const Coef<double> &k, void *snap,
+                        double2 *partials, const DevStatus *st, bool drho, bool epi, cudaStream_t s);
+    cudaError_t (*init_fields)(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
+                               const double *ux, const double *uy, void *snap, cudaStream_t s);
+    cudaError_t (*fields)(const void *src, const Grid &gd, const Coef<double> &k, double *rho, double *ux,
+                          double *uy, void *snap, cudaStream_t s);
+    cudaError_t (*set_pop)(void *dst, const Grid &gd, const Coef<double> &k, const double *f, cudaStream_t s);
+    cudaError_t (*get_pop)(const void *src, const Grid &gd, const Coef<double> &k, double *f, cudaStream_t s);
+    cudaError_t (*mass_partial)(const void *src, const Grid &gd, double2 *partials, cudaStream_t s);
+};
+
+extern const DtypeOps ops_f64, ops_f32, ops_f16;
+
+// grid of the tiled kernels
+inline dim3 step_grid(const Grid &gd) { return dim3((gd.nx + 31) / 32, (gd.ny + 7) / 8, 1); }
+
+}  // namespace prc

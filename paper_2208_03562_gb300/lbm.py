@@ -1,0 +1,327 @@
+"""Python binding of the C ABI in ``include/prc_lbm.h`` (``libprc_lbm.so``).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+the library.  Module-level functions carry the C names (``lbm_create``,
+``lbm_step``, ``lbm_run``, ``lbm_residual``, ``lbm_fields`` ...); the ``Lbm``
+class is a convenience wrapper around one handle.  Loading fails loudly when the
+library cannot be built or loaded -- there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32, F16 = 0, 1, 2
+DTYPE_CODES = {"f64": F64, "f32": F32, "f16": F16}
+BC_CAVITY, BC_CHANNEL, BC_PERIODIC = 0, 1, 2
+DRHO_CURRENT, DRHO_OFF = 0, 1
+
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTCONVERGED = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDIVERGED", "ETIMEOUT", "ENOTCONVERGED"]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
+                ("r", C.c_double), ("gamma", C.c_double), ("nu", C.c_double), ("u_lid", C.c_double),
+                ("omega_xi", C.c_double), ("fx", C.c_double), ("fy", C.c_double),
+                ("dtype", C.c_int32), ("bc", C.c_int32), ("drho", C.c_int32), ("reserved", C.c_int32)]
+
+
+class lbm_info_t(C.Structure):
+    _fields_ = [("step", C.c_int64), ("residual_step", C.c_int64), ("residual", C.c_double),
+                ("mass", C.c_double), ("converged", C.c_int32), ("diverged", C.c_int32)]
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+_H = C.c_void_p
+
+
+def load():
+    """Build (if stale) and load libprc_lbm.so; raise if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libprc_lbm.so missing at %s" % path)
+    L = C.CDLL(path)
+    P = C.POINTER(lbm_params)
+    sig = {
+        "lbm_params_init": [P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int],
+        "lbm_params_check": [P],
+        "lbm_workspace_bytes": [P, C.POINTER(C.c_size_t)],
+        "lbm_omega_nu": [P, _D],
+        "lbm_create": [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(_H)],
+        "lbm_create_p": [P, C.POINTER(_H)],
+        "lbm_create_ex": [P, C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(_H)],
+        "lbm_set_stream": [_H, C.c_void_p],
+        "lbm_step": [_H, C.c_long],
+        "lbm_run": [_H, C.c_double, C.c_long, C.POINTER(C.c_long)],
+        "lbm_residual": [_H, _D],
+        "lbm_mass": [_H, _D],
+        "lbm_info": [_H, C.POINTER(lbm_info_t)],
+        "lbm_sync": [_H],
+        "lbm_fields": [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
+        "lbm_init_fields": [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
+        "lbm_set_populations": [_H, C.c_void_p, C.c_int],
+        "lbm_get_populations": [_H, C.c_void_p, C.c_int],
+        "lbm_save_bytes": [_H, C.POINTER(C.c_size_t)],
+        "lbm_save": [_H, C.c_void_p, C.c_size_t],
+        "lbm_load": [_H, C.c_void_p, C.c_size_t],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.lbm_destroy.argtypes = [_H]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = [_H]
+    L.lbm_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the ``lbm_*`` entry points the loaded library resolves."""
+    L = load()
+    out = []
+    for name in ("lbm_params_init", "lbm_params_check", "lbm_workspace_bytes", "lbm_omega_nu", "lbm_create",
+                 "lbm_create_p", "lbm_create_ex", "lbm_set_stream", "lbm_destroy", "lbm_last_error",
+                 "lbm_step", "lbm_run", "lbm_residual", "lbm_mass", "lbm_info", "lbm_sync", "lbm_fields",
+                 "lbm_init_fields", "lbm_set_populations", "lbm_get_populations", "lbm_save_bytes",
+                 "lbm_save", "lbm_load"):
+        if hasattr(L, name):
+            out.append(name)
+    return out
+
+
+def _check(status, h=None):
+    if status != OK:
+        msg = load().lbm_last_error(h)
+        raise LbmError(status, msg.decode() if msg else "")
+    return status
+
+
+# ---------------------------------------------------------------------------
+# C-named functions
+
+def lbm_params_init(nx, ny, r, gamma, nu, u_lid, dtype=F32, bc=BC_CAVITY, drho=DRHO_CURRENT,
+                    omega_xi=1.0, fx=0.0, fy=0.0) -> lbm_params:
+    p = lbm_params()
+    _check(load().lbm_params_init(C.byref(p), nx, ny, r, gamma, nu, u_lid, dtype))
+    p.bc, p.drho, p.omega_xi, p.fx, p.fy = bc, drho, omega_xi, fx, fy
+    return p
+
+
+def lbm_params_check(p: lbm_params):
+    return _check(load().lbm_params_check(C.byref(p)))
+
+
+def lbm_workspace_bytes(p: lbm_params) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_workspace_bytes(C.byref(p), C.byref(n)))
+    return n.value
+
+
+def lbm_omega_nu(p: lbm_params) -> float:
+    w = C.c_double()
+    _check(load().lbm_omega_nu(C.byref(p), C.byref(w)))
+    return w.value
+
+
+def lbm_create(nx, ny, r, gamma, nu, u_lid, dtype=F32):
+    h = _H()
+    _check(load().lbm_create(nx, ny, r, gamma, nu, u_lid, dtype, C.byref(h)))
+    return h
+
+
+def lbm_create_p(p: lbm_params):
+    h = _H()
+    _check(load().lbm_create_p(C.byref(p), C.byref(h)))
+    return h
+
+
+def lbm_create_ex(p: lbm_params, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    h = _H()
+    _check(load().lbm_create_ex(C.byref(p), C.c_void_p(workspace_ptr), workspace_bytes,
+                                C.c_void_p(stream_ptr), C.byref(h)))
+    return h
+
+
+def lbm_destroy(h):
+    load().lbm_destroy(h)
+
+
+def lbm_step(h, n):
+    _check(load().lbm_step(h, int(n)), h)
+
+
+def lbm_run(h, tol, max_steps):
+    """Returns (status, steps_done); raises only on errors other than
+    ENOTCONVERGED."""
+    done = C.c_long()
+    s = load().lbm_run(h, float(tol), int(max_steps), C.byref(done))
+    if s not in (OK, ENOTCONVERGED):
+        _check(s, h)
+    return s, done.value
+
+
+def lbm_residual(h) -> float:
+    v = C.c_double()
+    _check(load().lbm_residual(h, C.byref(v)), h)
+    return v.value
+
+
+def lbm_mass(h) -> float:
+    v = C.c_double()
+    _check(load().lbm_mass(h, C.byref(v)), h)
+    return v.value
+
+
+def lbm_info(h) -> lbm_info_t:
+    info = lbm_info_t()
+    _check(load().lbm_info(h, C.byref(info)), h)
+    return info
+
+
+def lbm_sync(h):
+    _check(load().lbm_sync(h), h)
+
+
+def _host_ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def lbm_fields(h, ny, nx):
+    rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+    _check(load().lbm_fields(h, _host_ptr(rho), _host_ptr(ux), _host_ptr(uy), 0), h)
+    return rho, ux, uy
+
+
+def lbm_fields_device(h, rho_ptr, ux_ptr, uy_ptr):
+    _check(load().lbm_fields(h, C.c_void_p(rho_ptr), C.c_void_p(ux_ptr), C.c_void_p(uy_ptr), 1), h)
+
+
+def lbm_init_fields(h, rho, ux, uy):
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (rho, ux, uy)]
+    _check(load().lbm_init_fields(h, *[_host_ptr(v) for v in a], 0), h)
+
+
+def lbm_set_populations(h, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().lbm_set_populations(h, _host_ptr(f), 0), h)
+
+
+def lbm_get_populations(h, ny, nx):
+    f = np.empty((9, ny, nx))
+    _check(load().lbm_get_populations(h, _host_ptr(f), 0), h)
+    return f
+
+
+def lbm_save(h) -> bytes:
+    n = C.c_size_t()
+    _check(load().lbm_save_bytes(h, C.byref(n)), h)
+    buf = (C.c_char * n.value)()
+    _check(load().lbm_save(h, buf, n.value), h)
+    return bytes(buf)
+
+
+def lbm_load(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().lbm_load(h, buf, len(blob)), h)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+
+class Lbm:
+    """One PRC-LBM instance on the current CUDA device.
+
+    ``Lbm(params)`` lets the library own its memory and stream;
+    ``Lbm(params, torch_workspace=True)`` places every buffer in one PyTorch
+    uint8 tensor and enqueues on PyTorch's current stream.
+    """
+
+    def __init__(self, params: lbm_params, torch_workspace: bool = False):
+        self.p = params
+        self._ws = None
+        if torch_workspace:
+            import torch
+            nbytes = lbm_workspace_bytes(params)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            base = (base + 255) // 256 * 256
+            self.h = lbm_create_ex(params, base, nbytes, torch.cuda.current_stream().cuda_stream)
+        else:
+            self.h = lbm_create_p(params)
+
+    @classmethod
+    def cavity(cls, cav, bc=BC_CAVITY, drho=DRHO_CURRENT, **kw):
+        """From a ``inputs.Cavity`` workload description."""
+        p = lbm_params_init(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, DTYPE_CODES[cav.dtype],
+                            bc=bc, drho=drho)
+        return cls(p, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.p.ny, self.p.nx)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def run(self, tol, max_steps):
+        return lbm_run(self.h, tol, max_steps)
+
+    def residual(self):
+        return lbm_residual(self.h)
+
+    def mass(self):
+        return lbm_mass(self.h)
+
+    def info(self):
+        return lbm_info(self.h)
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def fields(self):
+        return lbm_fields(self.h, self.p.ny, self.p.nx)
+
+    def init_fields(self, rho, ux, uy):
+        shape = self.shape
+        lbm_init_fields(self.h, *[np.broadcast_to(v, shape) for v in (rho, ux, uy)])
+
+    def set_populations(self, f):
+        lbm_set_populations(self.h, np.reshape(f, (9,) + self.shape))
+
+    def populations(self):
+        return lbm_get_populations(self.h, self.p.ny, self.p.nx)
+
+    def save(self) -> bytes:
+        return lbm_save(self.h)
+
+    def load(self, blob: bytes):
+        lbm_load(self.h, blob)

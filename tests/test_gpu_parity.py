@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; populations and fields compared element by
+element.  Tolerances (relative L2 of the velocity over both components, or as
+stated per test): FP64 <= 1e-10, FP32 <= 1e-5 after 1000 steps, FP16 <= 1e-3
+at steady state.
+"""
+import numpy as np
+import pytest
+
+from oracle import stepper as S
+from paper_2208_03562_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+L = pytest.importorskip("paper_2208_03562_gb300.lbm")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    L.load()
+    S.num_threads(0)
+
+
+def pair(nx, ny, r=1.0, gamma=1.0, nu=0.05, u_lid=0.0, dtype=L.F64, bc=L.BC_CAVITY, drho=L.DRHO_CURRENT,
+         fx=0.0, fy=0.0, omega_xi=1.0, torch_ws=False):
+    p = L.lbm_params_init(nx, ny, r, gamma, nu, u_lid, dtype, bc=bc, drho=drho, omega_xi=omega_xi, fx=fx, fy=fy)
+    g = L.Lbm(p, torch_workspace=torch_ws)
+    o = S.Oracle(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u_lid, omega_xi=omega_xi,
+                                fx=fx, fy=fy, bc=bc, drho_off=int(drho == L.DRHO_OFF)))
+    return g, o
+
+
+def random_start(g, o, seed, amp=2e-3):
+    w = S.rest_weights(o.p)
+    f = w[:, None, None] + I.noise(seed, (9, o.p.ny, o.p.nx), amp)
+    o.set_populations(f)
+    g.set_populations(f)
+    return f
+
+
+def rel_l2_u(a, b):
+    num = np.sqrt(np.sum((a[1] - b[1]) ** 2 + (a[2] - b[2]) ** 2))
+    den = np.sqrt(np.sum(b[1] ** 2 + b[2] ** 2))
+    return num / den
+
+
+# ---------------------------------------------------------------------------
+# FP64: element-wise, tiny to multi-tile ragged grids, every boundary mode
+
+CASES = [
+    # nx, ny, r, gamma, nu, u_lid, bc, drho, fx, fy
+    (3, 3, 1.0, 1.0, 0.05, 0.05, L.BC_CAVITY, L.DRHO_CURRENT, 0.0, 0.0),
+    (5, 7, 0.5, 0.25, 0.01, 0.02, L.BC_CAVITY, L.DRHO_CURRENT, 0.0, 0.0),
+    (70, 19, 2.0, 0.1, 0.01, 0.02, L.BC_CAVITY, L.DRHO_CURRENT, 0.0, 0.0),
+    (70, 19, 0.25, 0.5, 0.002, 0.01, L.BC_CAVITY, L.DRHO_OFF, 0.0, 0.0),
+    (33, 9, 1.6, 0.05, 0.004, 0.005, L.BC_CHANNEL, L.DRHO_CURRENT, 1e-5, -2e-6),
+    (40, 17, 0.5, 1.0, 0.02, 0.0, L.BC_PERIODIC, L.DRHO_CURRENT, 3e-6, 1e-6),
+    (65, 33, 1.33, 0.3, 0.01, 0.03, L.BC_CHANNEL, L.DRHO_OFF, 0.0, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fp64_populations_match_oracle(case):
+    nx, ny, r, gamma, nu, u_lid, bc, drho, fx, fy = case
+    g, o = pair(nx, ny, r, gamma, nu, u_lid, L.F64, bc, drho, fx, fy)
+    random_start(g, o, seed=nx * 100 + ny)
+    for n in (1, 1, 5, 13, 40):
+        g.step(n)
+        o.step(n)
+        fg, fo = g.populations(), o.populations()
+        assert np.max(np.abs(fg - fo)) < 1e-13, (n, np.max(np.abs(fg - fo)))
+    a, b = g.fields(), o.fields()
+    assert rel_l2_u(a, b) < 1e-10
+    assert np.max(np.abs(a[0] - b[0])) < 1e-13
+
+
+def test_fp64_torch_workspace_and_stream():
+    g, o = pair(48, 20, 0.5, 0.2, 0.01, 0.02, L.F64, torch_ws=True)
+    random_start(g, o, seed=5)
+    g.step(60)
+    o.step(60)
+    assert np.max(np.abs(g.populations() - o.populations())) < 1e-13
+
+
+def test_fp64_init_fields_matches_oracle():
+    g, o = pair(37, 21, 2.0, 0.4, 0.01, 0.0, L.F64, bc=L.BC_PERIODIC)
+    rho, ux, uy = I.random_fields(3, 37, 21)
+    g.init_fields(rho, ux, uy)
+    o.init_fields(rho, ux, uy)
+    assert np.max(np.abs(g.populations() - o.populations())) < 1e-15
+    g.step(7)
+    o.step(7)
+    assert np.max(np.abs(g.populations() - o.populations())) < 1e-13
+
+
+def test_fp64_residual_and_mass_match_oracle():
+    g, o = pair(50, 30, 0.5, 0.25, 0.01, 0.03, L.F64)
+    m0 = o.total_mass()
+    for k in range(1, 6):
+        g.step(20)
+        o.step(20)
+        rg = g.residual()
+        ro = o.residual_update()
+        assert abs(rg - ro) <= 1e-9 * ro
+        info = g.info()
+        assert info.residual_step == 20 * k
+    assert abs(g.mass() - m0) < 1e-10
+    assert abs(g.mass() - o.total_mass()) < 1e-10
+
+
+def test_fp64_square_cavity_64_run_to_tolerance():
+    """64 x 64 square lattice, r = gamma = 1, Re = 100, U = 0.1, FP64, to
+    residual 1e-8 or 20000 steps: same step count and fields as the oracle."""
+    cav = I.square_cavity_64()
+    g, o = pair(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.F64)
+    st, steps_g = g.run(cav.tol, cav.max_steps)
+    steps_o, res_o = o.run(cav.tol, cav.max_steps)
+    assert steps_g == steps_o
+    assert (st == L.OK) == (res_o < cav.tol)
+    assert rel_l2_u(g.fields(), o.fields()) < 1e-10
+    assert abs(g.residual() - res_o) <= 1e-8 * res_o
+
+
+def test_checkpoint_resume_is_bitwise():
+    g, _ = pair(45, 23, 0.5, 0.5, 0.01, 0.02, L.F32)
+    g.step(77)
+    blob = g.save()
+    g.step(63)
+    a = g.populations()
+    ra = g.residual()
+    g.load(blob)
+    g.step(63)
+    assert np.array_equal(a, g.populations())
+    assert g.residual() == ra
+
+
+# ---------------------------------------------------------------------------
+# FP32 / FP16
+
+FP32_CASES = [
+    ("square cavity 64x64", I.square_cavity_64(), None),
+    ("deep cavity 128x128 r=2 gamma=0.1", I.deep_cavity_128(0.1), None),
+    ("512x128 cut of the 8192x2048 shallow cavity", I.shallow_cavity_8192x2048(), (512, 128)),
+]
+
+
+@pytest.mark.parametrize("name,cav,cut", FP32_CASES, ids=[c[0] for c in FP32_CASES])
+def test_fp32_after_1000_steps(name, cav, cut):
+    nx, ny = cut if cut else (cav.nx, cav.ny)
+    g, o = pair(nx, ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.F32)
+    g.step(1000)
+    o.step(1000)
+    e = rel_l2_u(g.fields(), o.fields())
+    assert e < 1e-5, e
+
+
+def test_fp16_steady_state():
+    """FP16 shifted storage, FP32 collision: steady shallow cavity."""
+    nx, ny, r, gamma, U, Re = 64, 32, 0.5, 0.25, 0.05, 100.0
+    nu = U * ny * r / Re
+    g16, o = pair(nx, ny, r, gamma, nu, U, L.F16)
+    o.run(1e-10, 400000)
+    st, steps = g16.run(1e-6, 400000)
+    e = rel_l2_u(g16.fields(), o.fields())
+    assert e < 1e-3, (e, st, steps)
+
+
+def test_full_size_shallow_cavity_fp32_sampled():
+    """The 8192 x 2048 workload in the launch configuration of the benchmark:
+    40 steps from rest, compared with the oracle on every node."""
+    cav = I.shallow_cavity_8192x2048("f32")
+    g, o = pair(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.F32, torch_ws=True)
+    g.step(40)
+    o.step(40)
+    a, b = g.fields(), o.fields()
+    assert rel_l2_u(a, b) < 1e-5
+    assert abs(g.mass() - o.total_mass()) < 1e-6 * cav.nodes
