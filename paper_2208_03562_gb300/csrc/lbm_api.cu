@@ -3,10 +3,13 @@
 // device-side stop rule of lbm_run, residual/mass finalisation, field and
 // population transfers, checkpoints.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+
+#include <cuda.h>
 
 #include "prc_lbm.h"
 #include "prc_ops.h"
@@ -14,6 +17,7 @@
 using prc::Coef;
 using prc::DevStatus;
 using prc::Grid;
+using prc::Plan;
 
 namespace {
 
@@ -34,6 +38,58 @@ const prc::DtypeOps *ops_for(int dtype)
     }
 }
 
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+void add_rect(prc::Rects &rc, int x0, int y0, int x1, int y1)
+{
+    if (x1 <= x0 || y1 <= y0) return;
+    const int i = rc.n++;
+    rc.x0[i] = x0;
+    rc.y0[i] = y0;
+    rc.x1[i] = x1;
+    rc.y1[i] = y1;
+    rc.tiles_x[i] = ceil_div(x1 - x0, prc::BX);
+    rc.start[i + 1] = rc.start[i] + rc.tiles_x[i] * ceil_div(y1 - y0, prc::BY);
+}
+
+// Split of one step between the TMA interior kernel (tiles at least two nodes
+// from every wall, x origin 16-byte aligned) and the general kernel on the
+// remaining edge strips.  num_sms <= 0 gives the upper bound used to size the
+// workspace.
+Plan make_plan(const lbm_params &p, int num_sms)
+{
+    const prc::DtypeOps *ops = ops_for(p.dtype);
+    Plan pl;
+    std::memset(&pl, 0, sizeof(pl));
+    const int W = ops->tma_w, H = ops->tma_h, PX = ops->tma_padx;
+    const int ix0 = PX, iy0 = 2;
+    if (W > 0 && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
+        const int xlast = ((p.nx - 2 - W) / PX) * PX;
+        const int ylast = p.ny - 2 - H;
+        const int xend = xlast + W, yend = ylast + H;
+        pl.tma = 1;
+        pl.in.ix0 = ix0;
+        pl.in.iy0 = iy0;
+        pl.in.ntx = ceil_div(xend - ix0, W);
+        pl.in.nty = ceil_div(yend - iy0, H);
+        pl.in.xlast = xlast;
+        pl.in.ylast = ylast;
+        const int ntiles = pl.in.ntx * pl.in.nty;
+        int g = ntiles < prc::MAX_INTERIOR_CTAS ? ntiles : prc::MAX_INTERIOR_CTAS;
+        if (num_sms > 0 && g > num_sms) g = num_sms;
+        pl.n_int_ctas = g;
+        add_rect(pl.edge, 0, 0, p.nx, iy0);
+        add_rect(pl.edge, 0, yend, p.nx, p.ny);
+        add_rect(pl.edge, 0, iy0, ix0, yend);
+        add_rect(pl.edge, xend, iy0, p.nx, yend);
+    } else {
+        add_rect(pl.edge, 0, 0, p.nx, p.ny);
+    }
+    pl.n_edge_ctas = pl.edge.start[pl.edge.n];
+    pl.nparts = pl.n_int_ctas + pl.n_edge_ctas;
+    return pl;
+}
+
 struct Layout {
     int pitch;
     size_t plane, pop_bytes, snap_bytes, part_bytes, st_bytes;
@@ -49,7 +105,9 @@ Layout make_layout(const lbm_params &p)
     L.plane = (size_t)L.pitch * (size_t)p.ny;
     L.pop_bytes = align_up(9 * L.plane * ops->elem, ALIGN);
     L.snap_bytes = align_up(L.plane * ops->snap_elem, ALIGN);
-    L.nparts = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    const int mass_parts = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    const int step_parts = make_plan(p, 0).nparts;
+    L.nparts = mass_parts > step_parts ? mass_parts : step_parts;
     L.part_bytes = align_up((size_t)L.nparts * sizeof(double2), ALIGN);
     L.st_bytes = align_up(sizeof(DevStatus), ALIGN);
     L.off_pop0 = 0;
@@ -229,6 +287,8 @@ struct lbm_s {
     DevStatus *st;
     DevStatus *st_host;  // pinned mirror
     long long t;         // completed steps; invariant: the state is in pop[t & 1]
+    Plan plan;
+    CUtensorMap tmap[2];  // TMA descriptors of the two population sets
     cudaGraphExec_t g20;
     bool have_g20;
     std::string err;
@@ -269,10 +329,10 @@ lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
 {
     const bool epi = ((t_before + 1) % RES_INTERVAL) == 0;
     const int c = (int)(t_before & 1);
-    CK(h, h->ops->step(h->pop[c], h->pop[c ^ 1], h->gd, h->k, h->snap, h->partials, h->st,
-                       h->p.drho == LBM_DRHO_CURRENT, epi, s));
+    CK(h, h->ops->step(h->pop[c], h->pop[c ^ 1], h->plan.tma ? &h->tmap[c] : nullptr, h->plan, h->gd, h->k,
+                       h->snap, h->partials, h->st, h->p.drho == LBM_DRHO_CURRENT, epi, s));
     if (epi) {
-        k_finalize<<<1, 256, 0, s>>>(h->partials, h->L.nparts, h->st, (double)h->p.nx * (double)h->p.ny);
+        k_finalize<<<1, 256, 0, s>>>(h->partials, h->plan.nparts, h->st, (double)h->p.nx * (double)h->p.ny);
         CK(h, cudaGetLastError());
     }
     return LBM_OK;
@@ -350,6 +410,39 @@ struct DevTmp {
     }
 };
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 3-D tiled descriptor over one population set: (x < nx, y < ny, plane < 9),
+// box = interior tile + ring, x widened to 16-byte aligned edges.
+lbm_status make_tmaps(lbm_t h)
+{
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled not available");
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    const size_t elem = h->ops->elem;
+    const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : (elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const cuuint64_t dims[3] = {(cuuint64_t)h->p.nx, (cuuint64_t)h->p.ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * elem, (cuuint64_t)h->L.plane * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)(h->ops->tma_w + 2 * h->ops->tma_padx), (cuuint32_t)(h->ops->tma_h + 2), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int b = 0; b < 2; b++) {
+        CUresult r = encode(&h->tmap[b], dt, 3, h->pop[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    }
+    return LBM_OK;
+}
+
 lbm_status init_handle(lbm_t h, const lbm_params &p, void *ws, size_t ws_bytes, bool own_ws, cudaStream_t stream,
                        bool own_stream)
 {
@@ -370,6 +463,23 @@ lbm_status init_handle(lbm_t h, const lbm_params &p, void *ws, size_t ws_bytes, 
     h->st = reinterpret_cast<DevStatus *>(h->ws + h->L.off_st);
     h->t = 0;
     h->have_g20 = false;
+    int nsm = 0;
+    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    h->plan = make_plan(p, nsm);
+    // PRC_LBM_GENERAL_ONLY=1 runs every node through the general kernel (for
+    // comparing the two code paths)
+    const char *gen = std::getenv("PRC_LBM_GENERAL_ONLY");
+    if (gen && gen[0] == '1') {
+        lbm_params q = p;
+        q.dtype = LBM_F64;  // the FP64 table has no interior tile
+        Plan g = make_plan(q, nsm);
+        h->plan = g;
+    }
+    if (h->plan.tma) {
+        lbm_status ts = make_tmaps(h);
+        if (ts != LBM_OK) return ts;
+        CK(h, h->ops->prepare());
+    }
     CK(h, cudaMallocHost(&h->st_host, sizeof(DevStatus)));
     // rest state f~ = w(r): zero shifted storage everywhere (padding too)
     CK(h, cudaMemsetAsync(h->ws, 0, h->L.off_part, h->stream));

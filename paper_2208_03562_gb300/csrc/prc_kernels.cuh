@@ -3,6 +3,7 @@
 #pragma once
 
 #include "prc_device.cuh"
+#include "prc_reduce.cuh"
 
 namespace prc {
 
@@ -10,46 +11,34 @@ constexpr int BX = 32;  // tile width  (nodes, one per thread)
 constexpr int BY = 8;   // tile height
 constexpr int NRING = 2 * (BX + 2) + 2 * BY;
 
-// Warp-shuffle then CTA reduction of two FP64 sums; thread 0 gets the totals.
-__device__ __forceinline__ void block_sum2(double &a, double &b, double *sm /* 2 * nwarps */)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nw = (blockDim.x * blockDim.y) >> 5;
-    if ((tid & 31) == 0) {
-        sm[tid >> 5] = a;
-        sm[nw + (tid >> 5)] = b;
-    }
-    __syncthreads();
-    if (tid < 32) {
-        a = tid < nw ? sm[tid] : 0.0;
-        b = tid < nw ? sm[nw + tid] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-    }
-}
+// Rectangles of nodes handled by the general kernel (the whole domain, or the
+// edge strips around the interior tiles of the TMA kernel), enumerated as a
+// 1-D list of BX x BY tiles.
+struct Rects {
+    int n;
+    int x0[4], y0[4], x1[4], y1[4];
+    int tiles_x[4];
+    int start[5];  // first tile index of each rectangle; start[n] = total
+};
 
-// One fused time step: pull-stream + walls, density tile (+1 ring) in shared
-// memory for the density gradient, collision, store.  With EPI the step also
-// evaluates (u_x - u_x,snapshot)^2 and drho per CTA in FP64 for the residual
-// of Sec. 5.2 and refreshes the snapshot.
+// One fused time step on the nodes of `rc`: pull-stream + walls, density tile
+// (+1 ring) in shared memory for the density gradient, collision, store.  With
+// EPI the step also accumulates (u_x - u_x,snapshot)^2 and drho per CTA for the
+// residual of Sec. 5.2 and refreshes the snapshot; the CTA totals go to
+// partials[part0 + blockIdx.x].
 template <typename S, typename T, bool DRHO, bool EPI>
 __global__ void __launch_bounds__(BX * BY)
 k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
-       double2 *__restrict__ partials, const DevStatus *__restrict__ st)
+       double2 *__restrict__ partials, const DevStatus *__restrict__ st, Rects rc, int part0)
 {
     if (st->stop) return;
+    int r = 0;
+    while (r + 1 < rc.n && (int)blockIdx.x >= rc.start[r + 1]) r++;
+    const int lt = blockIdx.x - rc.start[r];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x0 = rc.x0[r] + (lt % rc.tiles_x[r]) * BX, y0 = rc.y0[r] + (lt / rc.tiles_x[r]) * BY;
     const int x = x0 + tx, y = y0 + ty;
-    const bool valid = (x < gd.nx) & (y < gd.ny);
+    const bool valid = (x < rc.x1[r]) & (y < rc.y1[r]);
 
     T g[9];
     int mx = x, my = y;
@@ -91,17 +80,17 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
         for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>(g[i]);
     }
     if constexpr (EPI) {
-        __shared__ double sm[2 * (BX * BY / 32)];
-        double d2 = 0.0, dm = 0.0;
+        __shared__ double red[2 * (BX * BY / 32)];
+        RedAcc<T> acc;
         if (valid) {
             const long long o = (long long)y * gd.pitch + x;
-            const double d = (double)ux - (double)snap[o];
+            const T d = ux - snap[o];
             snap[o] = ux;
-            d2 = d * d;
-            dm = (double)drho;
+            acc.add(d * d, drho);
         }
-        block_sum2(d2, dm, sm);
-        if (ty == 0 && tx == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(d2, dm);
+        double a, b;
+        acc.block_total(a, b, red);
+        if (ty == 0 && tx == 0) partials[part0 + blockIdx.x] = make_double2(a, b);
     }
 }
 
@@ -200,9 +189,12 @@ __global__ void __launch_bounds__(BX * BY) k_mass_partial(const S *__restrict__ 
 #pragma unroll
         for (int i = 0; i < 9; i++) dm += (double)ld_s<S, T>(src + (long long)i * gd.plane + o);
     }
-    __shared__ double sm[2 * (BX * BY / 32)];
-    block_sum2(z, dm, sm);
-    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(z, dm);
+    __shared__ double red[2 * (BX * BY / 32)];
+    RedAcc<double> acc;
+    acc.add(z, dm);
+    double a, b;
+    acc.block_total(a, b, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = make_double2(a, b);
 }
 
 }  // namespace prc

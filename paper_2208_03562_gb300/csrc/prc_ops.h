@@ -3,8 +3,11 @@
 // ops_f16.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
-#include "prc_device.cuh"
+
+#include "prc_kernels.cuh"
+#include "prc_tma.cuh"
 
 namespace prc {
 
@@ -18,11 +21,27 @@ inline Coef<T> cast_coef(const Coef<double> &d)
     return c;
 }
 
+// How one time step is split between the TMA interior kernel and the general
+// (wall-aware) kernel on the remaining edge strips.
+struct Plan {
+    int tma;           // interior kernel in use
+    Interior in;
+    int n_int_ctas;    // persistent grid of the interior kernel; partials [0, n_int_ctas)
+    Rects edge;        // rectangles of the general kernel
+    int n_edge_ctas;   // partials [n_int_ctas, n_int_ctas + n_edge_ctas)
+    int nparts;
+};
+
+constexpr int MAX_INTERIOR_CTAS = 1024;
+
 struct DtypeOps {
     size_t elem;       // bytes per stored population
     size_t snap_elem;  // bytes per snapshot value (collision precision)
-    cudaError_t (*step)(const void *src, void *dst, const Grid &gd, const Coef<double> &k, void *snap,
-                        double2 *partials, const DevStatus *st, bool drho, bool epi, cudaStream_t s);
+    int tma_w, tma_h, tma_padx;  // interior tile (0: no TMA path)
+    cudaError_t (*prepare)();
+    cudaError_t (*step)(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
+                        const Coef<double> &k, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
+                        cudaStream_t s);
     cudaError_t (*init_fields)(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
                                const double *ux, const double *uy, void *snap, cudaStream_t s);
     cudaError_t (*fields)(const void *src, const Grid &gd, const Coef<double> &k, double *rho, double *ux,

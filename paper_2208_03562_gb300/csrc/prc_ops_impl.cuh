@@ -3,7 +3,6 @@
 // PRC_S (storage type), PRC_T (collision type) and PRC_OPS (table name).
 #pragma once
 
-#include "prc_kernels.cuh"
 #include "prc_ops.h"
 
 namespace prc {
@@ -11,23 +10,74 @@ namespace {
 
 using S = PRC_S;
 using T = PRC_T;
+constexpr int TW = PRC_TMA_W, TH = PRC_TMA_H;
 
-cudaError_t op_step(const void *src, void *dst, const Grid &gd, const Coef<double> &kd, void *snap,
-                    double2 *partials, const DevStatus *st, bool drho, bool epi, cudaStream_t s)
+template <bool DRHO, bool EPI>
+cudaError_t launch_tma(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn,
+                       double2 *partials, DevStatus *st, cudaStream_t s)
+{
+    if constexpr (TW > 0) {
+        using Cf = TmaCfg<S, TW, TH>;
+        k_step_tma<S, T, TW, TH, DRHO, EPI><<<pl.n_int_ctas, Cf::THREADS, Cf::SMEM, s>>>(*tsrc, b, gd, k, sn,
+                                                                                        partials, st, pl.in);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+// opt the interior kernels into their dynamic shared memory (once, outside
+// any stream capture)
+cudaError_t op_prepare()
+{
+    if constexpr (TW > 0) {
+        using Cf = TmaCfg<S, TW, TH>;
+        cudaError_t e;
+        if ((e = cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, true, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, true, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM);
+    }
+    return cudaSuccess;
+}
+
+template <bool DRHO, bool EPI>
+cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn,
+                           double2 *partials, const DevStatus *st, cudaStream_t s)
+{
+    k_step<S, T, DRHO, EPI><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st, pl.edge,
+                                                                    pl.n_int_ctas);
+    return cudaGetLastError();
+}
+
+template <bool DRHO, bool EPI>
+cudaError_t step_both(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
+                      const Coef<T> &k, T *sn, double2 *partials, DevStatus *st, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (pl.tma) e = launch_tma<DRHO, EPI>(tsrc, static_cast<S *>(dst), pl, gd, k, sn, partials, st, s);
+    if (e == cudaSuccess && pl.n_edge_ctas > 0)
+        e = launch_general<DRHO, EPI>(static_cast<const S *>(src), static_cast<S *>(dst), pl, gd, k, sn, partials,
+                                      st, s);
+    return e;
+}
+
+cudaError_t op_step(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
+                    const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
+                    cudaStream_t s)
 {
     const Coef<T> k = cast_coef<T>(kd);
-    const dim3 grid = step_grid(gd), block(BX, BY);
-    const S *a = static_cast<const S *>(src);
-    S *b = static_cast<S *>(dst);
     T *sn = static_cast<T *>(snap);
     if (drho) {
-        if (epi) k_step<S, T, true, true><<<grid, block, 0, s>>>(a, b, gd, k, sn, partials, st);
-        else k_step<S, T, true, false><<<grid, block, 0, s>>>(a, b, gd, k, sn, partials, st);
-    } else {
-        if (epi) k_step<S, T, false, true><<<grid, block, 0, s>>>(a, b, gd, k, sn, partials, st);
-        else k_step<S, T, false, false><<<grid, block, 0, s>>>(a, b, gd, k, sn, partials, st);
+        if (epi) return step_both<true, true>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
+        return step_both<true, false>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
     }
-    return cudaGetLastError();
+    if (epi) return step_both<false, true>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
+    return step_both<false, false>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
 }
 
 dim3 row_grid(const Grid &gd) { return dim3((gd.nx + 127) / 128, gd.ny, 1); }
@@ -68,7 +118,8 @@ cudaError_t op_mass_partial(const void *src, const Grid &gd, double2 *partials, 
 
 }  // namespace
 
-const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), op_step, op_init_fields, op_fields, op_set_pop, op_get_pop,
+const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), TW, TH, TW > 0 ? 16 / (int)sizeof(S) : 0,
+                          op_prepare, op_step, op_init_fields, op_fields, op_set_pop, op_get_pop,
                           op_mass_partial};
 
 }  // namespace prc

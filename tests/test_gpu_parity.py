@@ -5,6 +5,8 @@ element.  Tolerances (relative L2 of the velocity over both components, or as
 stated per test): FP64 <= 1e-10, FP32 <= 1e-5 after 1000 steps, FP16 <= 1e-3
 at steady state.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -97,9 +99,13 @@ def test_fp64_init_fields_matches_oracle():
     assert np.max(np.abs(g.populations() - o.populations())) < 1e-13
 
 
+def oracle_mass(o):
+    return math.fsum(o.populations().ravel())
+
+
 def test_fp64_residual_and_mass_match_oracle():
     g, o = pair(50, 30, 0.5, 0.25, 0.01, 0.03, L.F64)
-    m0 = o.total_mass()
+    m0 = oracle_mass(o)
     for k in range(1, 6):
         g.step(20)
         o.step(20)
@@ -108,8 +114,8 @@ def test_fp64_residual_and_mass_match_oracle():
         assert abs(rg - ro) <= 1e-9 * ro
         info = g.info()
         assert info.residual_step == 20 * k
-    assert abs(g.mass() - m0) < 1e-10
-    assert abs(g.mass() - o.total_mass()) < 1e-10
+    assert abs(g.mass() - m0) < 1e-11
+    assert abs(g.mass() - oracle_mass(o)) < 1e-11
 
 
 def test_fp64_square_cavity_64_run_to_tolerance():
@@ -122,7 +128,9 @@ def test_fp64_square_cavity_64_run_to_tolerance():
     assert steps_g == steps_o
     assert (st == L.OK) == (res_o < cav.tol)
     assert rel_l2_u(g.fields(), o.fields()) < 1e-10
-    assert abs(g.residual() - res_o) <= 1e-8 * res_o
+    # the converged residual is a norm of differences of O(0.1) velocities:
+    # FP64 round-off leaves ~1e-7 relative agreement at 1e-8
+    assert abs(g.residual() - res_o) <= 1e-6 * res_o
 
 
 def test_checkpoint_resume_is_bitwise():
@@ -139,7 +147,60 @@ def test_checkpoint_resume_is_bitwise():
 
 
 # ---------------------------------------------------------------------------
-# FP32 / FP16
+# FP32 / FP16: the TMA interior kernel + edge strips
+
+TMA_CASES = [
+    # nx, ny, r, gamma, nu, u_lid, bc, drho
+    (200, 100, 0.5, 0.25, 0.01, 0.03, L.BC_CAVITY, L.DRHO_CURRENT),
+    (301, 77, 2.0, 0.4, 0.01, 0.02, L.BC_CAVITY, L.DRHO_CURRENT),
+    (137, 45, 1.0, 1.0, 0.02, 0.05, L.BC_CHANNEL, L.DRHO_OFF),
+    (266, 134, 0.25, 0.6, 0.002, 0.01, L.BC_PERIODIC, L.DRHO_CURRENT),
+    (72, 38, 1.6, 0.2, 0.005, 0.01, L.BC_CAVITY, L.DRHO_CURRENT),
+]
+
+
+@pytest.mark.parametrize("case", TMA_CASES)
+@pytest.mark.parametrize("dtype", [L.F32, L.F16])
+def test_interior_kernel_matches_oracle(case, dtype):
+    nx, ny, r, gamma, nu, u_lid, bc, drho = case
+    g, o = pair(nx, ny, r, gamma, nu, u_lid, dtype, bc, drho)
+    random_start(g, o, seed=nx + ny, amp=1e-3)
+    w = S.rest_weights(o.p)[:, None, None]
+    tol = 2e-7 if dtype == L.F32 else 2e-5
+    for n in (1, 1, 18, 20):
+        g.step(n)
+        o.step(n)
+        dg, do = g.populations() - w, o.populations() - w
+        assert np.max(np.abs(dg - do)) < tol * max(1.0, n / 4), (n, np.max(np.abs(dg - do)))
+    a, b = g.fields(), o.fields()
+    assert rel_l2_u(a, b) < (1e-5 if dtype == L.F32 else 1e-3)
+
+
+def test_interior_and_general_paths_agree(monkeypatch):
+    """The TMA interior kernel and the general kernel run the same collision;
+    on the same input they agree to FP32 round-off."""
+    out = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("PRC_LBM_GENERAL_ONLY", env)
+        g, o = pair(330, 140, 0.5, 0.3, 0.01, 0.04, L.F32)
+        random_start(g, o, seed=9, amp=1e-3)
+        g.step(45)
+        out.append((g.populations(), g.residual()))
+    assert np.max(np.abs(out[0][0] - out[1][0])) < 1e-7
+    assert abs(out[0][1] - out[1][1]) <= 1e-5 * out[1][1]
+
+
+def test_fp32_residual_matches_oracle():
+    g, o = pair(260, 120, 0.5, 0.25, 0.01, 0.03, L.F32)
+    for k in range(1, 6):
+        g.step(20)
+        o.step(20)
+        rg, ro = g.residual(), o.residual_update()
+        assert abs(rg - ro) <= 1e-4 * ro, (k, rg, ro)
+
+
+# ---------------------------------------------------------------------------
+# FP32 / FP16 runs
 
 FP32_CASES = [
     ("square cavity 64x64", I.square_cavity_64(), None),
@@ -156,6 +217,20 @@ def test_fp32_after_1000_steps(name, cav, cut):
     o.step(1000)
     e = rel_l2_u(g.fields(), o.fields())
     assert e < 1e-5, e
+
+
+def test_deep_cavity_as_stated_diverges_on_both_sides():
+    """U = 0.05 with gamma = 0.1 on the r = 2 deep cavity: the oracle blows
+    up; the GPU run must stop and report EDIVERGED instead of hanging or
+    returning garbage."""
+    cav = I.deep_cavity_128_as_stated(0.1)
+    g, o = pair(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.F32)
+    steps_o, res_o = o.run(1e-7, 2000)
+    assert not np.isfinite(res_o)
+    with pytest.raises(L.LbmError) as e:
+        g.run(1e-7, 2000)
+    assert e.value.status == L.EDIVERGED
+    assert g.info().diverged == 1
 
 
 def test_fp16_steady_state():
@@ -178,4 +253,4 @@ def test_full_size_shallow_cavity_fp32_sampled():
     o.step(40)
     a, b = g.fields(), o.fields()
     assert rel_l2_u(a, b) < 1e-5
-    assert abs(g.mass() - o.total_mass()) < 1e-6 * cav.nodes
+    assert abs(g.mass() - oracle_mass(o)) < 1e-6 * cav.nodes
