@@ -127,7 +127,8 @@ double omega_nu_of(const lbm_params &p)
     return 1.0 / (p.nu / (p.gamma * c2) + 0.5);
 }
 
-// Per-instance constants (App. A coefficients with dt = 1).
+// Per-instance constants (App. A coefficients with dt = 1), in the folded
+// form the device collision uses.
 void make_coef(const lbm_params &p, Coef<double> &k)
 {
     std::memset(&k, 0, sizeof(k));
@@ -135,25 +136,19 @@ void make_coef(const lbm_params &p, Coef<double> &k)
     const double w_nu = omega_nu_of(p), w_xi = p.omega_xi;
     const double tau_nu = 1.0 / w_nu - 0.5, tau_xi = 1.0 / w_xi - 0.5;
     const double Pg = 4.0 / (g * g) - 1.0 / g, Qg = 1.0 / (g * g) - 1.0 / g, Ug = 2.0 / g + 1.0;
+    const double a3 = 1.0 / (g * g) - 3.0 / g + 2.0;
     k.r = r;
     k.r2 = r * r;
-    k.inv_r = 1.0 / r;
-    k.inv_r2 = 1.0 / (r * r);
     k.c2 = c2;
     k.c4 = c2 * c2;
-    k.w_nu = w_nu;
-    k.w_xi = w_xi;
-    k.one_m_w_nu = 1.0 - w_nu;
-    k.one_m_w_xi = 1.0 - w_xi;
-    k.src_nu = 1.0 - 0.5 * w_nu;
-    k.src_xi = 1.0 - 0.5 * w_xi;
-    k.m2tau_nu = -2.0 * tau_nu;
-    k.m2tau_xi = -2.0 * tau_xi;
-    k.mtau_nu = -tau_nu;
     k.ig = 1.0 / g;
     k.h1 = 1.0 / g - 1.0;
-    k.a3 = 1.0 / (g * g) - 3.0 / g + 2.0;
-    k.Pg = Pg;
+    k.hh1 = 0.5 * k.h1;
+    k.one_m_w_nu = 1.0 - w_nu;
+    k.hxi = 0.5 * (1.0 - w_xi);
+    k.hnu = 0.5 * (1.0 - w_nu);
+    k.kxs = -w_xi * tau_xi;
+    k.kd = -w_nu * tau_nu;
     k.Qg = Qg;
     k.hPg = 0.5 * Pg;
     k.hQg = 0.5 * Qg;
@@ -164,12 +159,26 @@ void make_coef(const lbm_params &p, Coef<double> &k)
     k.Cb0 = -2.0 * c2 / w_xi;
     k.Cs0 = -2.0 * c2 / w_nu;
     k.h1c2 = (1.0 / g - 1.0) * c2;
+    k.a3p1 = a3 + 1.0;
+    k.a34p1 = 4.0 * a3 + 1.0;
+    k.qr = 0.25 / r;
+    k.qr2 = 0.25 / (r * r);
+    k.hr = 0.5 / r;
+    k.hr2 = 0.5 / (r * r);
+    k.inv_r2 = 1.0 / (r * r);
     k.hx = p.fx / (2.0 * g);
     k.hy = p.fy / (2.0 * g);
-    k.twoQFx = 2.0 * Qg * p.fx;
-    k.twoQFy = 2.0 * Qg * p.fy;
-    k.QFx = Qg * p.fx;
-    k.QFy = Qg * p.fy;
+    k.fsx = (1.0 - 0.5 * w_xi) * Qg * p.fx;
+    k.fsy = (1.0 - 0.5 * w_xi) * Qg * p.fy;
+    k.fdx = (1.0 - 0.5 * w_nu) * Qg * p.fx;
+    k.fdy = (1.0 - 0.5 * w_nu) * Qg * p.fy;
+    k.nig = -k.ig;
+    k.nr2 = -k.r2;
+    k.nhPg = -k.hPg;
+    k.nhQg = -k.hQg;
+    k.nk3y = -k.k3y;
+    k.ninv_r2 = -k.inv_r2;
+    k.nfdy = -k.fdy;
     const bool lid_on = (p.bc != LBM_BC_PERIODIC) && (p.u_lid != 0.0);
     k.lid = lid_on ? c2 * p.u_lid / (2.0 * r * r) : 0.0;
     k.inv12 = 1.0 / 12.0;
@@ -330,7 +339,8 @@ lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
     const bool epi = ((t_before + 1) % RES_INTERVAL) == 0;
     const int c = (int)(t_before & 1);
     CK(h, h->ops->step(h->pop[c], h->pop[c ^ 1], h->plan.tma ? &h->tmap[c] : nullptr, h->plan, h->gd, h->k,
-                       h->snap, h->partials, h->st, h->p.drho == LBM_DRHO_CURRENT, epi, s));
+                       h->snap, h->partials, h->st, h->p.drho == LBM_DRHO_CURRENT, epi,
+                       h->p.fx != 0.0 || h->p.fy != 0.0, s));
     if (epi) {
         k_finalize<<<1, 256, 0, s>>>(h->partials, h->plan.nparts, h->st, (double)h->p.nx * (double)h->p.ny);
         CK(h, cudaGetLastError());

@@ -25,31 +25,33 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "prc_vec.cuh"
+
 namespace prc {
 
 // Per-instance constants, precomputed on the host in FP64 and cast to the
-// collision precision T.
+// collision type T (float, double, or F2 with both lanes equal).
 template <typename T>
 struct Coef {
-    T r, r2, inv_r, inv_r2;   // aspect ratio r = dy/dx and powers
-    T c2, c4;                 // c^2 = q^2 c_s*^2, q = min(1, r) (Eq. 2)
-    T w_nu, w_xi;             // shear / bulk relaxation rates
-    T one_m_w_nu, one_m_w_xi; // 1 - omega
-    T src_nu, src_xi;         // 1 - omega / 2
-    T m2tau_nu, m2tau_xi;     // -2 (1/omega - 1/2)
-    T mtau_nu;                // -(1/omega_nu - 1/2)
-    T ig, h1, a3, Pg, Qg;     // 1/g, 1/g - 1, 1/g^2 - 3/g + 2, P_gamma, Q_gamma
-    T hPg, hQg;               // P_gamma / 2, Q_gamma / 2
-    T Ax, By;                 // A = Ax u_x, B = By u_y (Eq. 43)
-    T k3x, k3y;               // (3c^2 - 1)/2, (3c^2 - r^2)/2
-    T Cb0, Cs0;               // -2 c^2 / omega_xi, -2 c^2 / omega_nu
-    T h1c2;                   // (1/g - 1) c^2
-    T hx, hy;                 // F / (2 gamma): half-force velocity shift
-    T twoQFx, twoQFy;         // 2 Q_gamma F (source moments, Eq. 13-central)
-    T QFx, QFy;               // Q_gamma F
-    T lid;                    // c^2 U / (2 r^2): moving-lid bounce-back term
-    T inv12, inv12r;          // 1/12, 1/(12 r): density-gradient stencil
-    T w[9];                   // rest populations w_i(r)
+    T r, r2;                   // aspect ratio r = dy/dx, r^2
+    T c2, c4;                  // c^2 = q^2 c_s*^2, q = min(1, r) (Eq. 2); c^4
+    T ig, h1, hh1;             // 1/g, 1/g - 1, (1/g - 1)/2
+    T one_m_w_nu;              // 1 - omega_nu
+    T hxi, hnu;                // (1 - omega_xi)/2, (1 - omega_nu)/2
+    T kxs, kd;                 // -omega_xi tau_xi, -omega_nu tau_nu (tau = 1/omega - 1/2)
+    T Qg, hPg, hQg;            // Q_gamma, P_gamma / 2, Q_gamma / 2
+    T Ax, By;                  // A = Ax u_x, B = By u_y (Eq. 43)
+    T k3x, k3y;                // (3c^2 - 1)/2, (3c^2 - r^2)/2
+    T Cb0, Cs0;                // -2 c^2 / omega_xi, -2 c^2 / omega_nu
+    T h1c2;                    // (1/g - 1) c^2
+    T a3p1, a34p1;             // a3 + 1, 4 a3 + 1 with a3 = 1/g^2 - 3/g + 2
+    T qr, qr2, hr, hr2, inv_r2;  // 1/(4r), 1/(4r^2), 1/(2r), 1/(2r^2), 1/r^2
+    T hx, hy;                  // F / (2 gamma): half-force velocity shift
+    T fsx, fsy, fdx, fdy;      // (1 - omega/2) Q_gamma F: source moments (Eq. 13-central)
+    T nig, nr2, nhPg, nhQg, nk3y, ninv_r2, nfdy;  // negated copies
+    T lid;                     // c^2 U / (2 r^2): moving-lid bounce-back term
+    T inv12, inv12r;           // 1/12, 1/(12 r): density-gradient stencil
+    T w[9];                    // rest populations w_i(r)
 };
 
 struct Grid {
@@ -90,9 +92,6 @@ template <> __device__ __forceinline__ double to_s<double, double>(double v) { r
 template <> __device__ __forceinline__ float to_s<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __half to_s<__half, float>(float v) { return __float2half_rn(v); }
 
-template <typename T> __device__ __forceinline__ T rcp(T v);
-template <> __device__ __forceinline__ double rcp<double>(double v) { return 1.0 / v; }
-template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
 
 // Map a node coordinate to the node whose density stands in for it (reading
 // A1: nearest fluid node across a wall, wrap across a periodic direction).
@@ -131,109 +130,133 @@ __device__ __forceinline__ void pull9(const S *__restrict__ src, const Grid &gd,
 }
 
 template <typename T>
-__device__ __forceinline__ T sum9(const T g[9])
+PRC_HD T sum9(const T g[9])
 {
-    return ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    return vadd(vadd(vadd(vadd(g[0], g[1]), vadd(g[2], g[3])), vadd(vadd(g[4], g[5]), vadd(g[6], g[7]))), g[8]);
 }
 
-// The collision in deviation form.  In: g[9] streamed shifted populations,
-// density gradient (dxr, dyr).  Out: g[9] post-collision shifted populations;
-// u_x, u_y, drho of the node.
-template <typename T, bool DRHO>
-__device__ __forceinline__ void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out, T &drho_out)
+// The collision in deviation form (App. A with the algebra rearranged as in
+// the file header), generic over float, double and packed F2.
+// In: g[9] streamed shifted populations, density gradient (dxr, dyr).
+// Out: g[9] post-collision shifted populations; u_x, u_y, drho of the node.
+template <typename T, bool DRHO, bool FORCE>
+PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out, T &drho_out)
 {
     // square-lattice raw moments of the deviations (Eq. 62 applied to g)
-    const T s00 = sum9(g);
-    const T s10 = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const T s01 = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-    const T d58 = (g[5] + g[6]) + (g[7] + g[8]);
-    const T s20 = (g[1] + g[3]) + d58;
-    const T s02 = (g[2] + g[4]) + d58;
-    const T s11 = (g[5] - g[6]) + (g[7] - g[8]);
+    const T a13 = vsub(g[1], g[3]), a56 = vsub(g[5], g[6]), a87 = vsub(g[8], g[7]);
+    const T p13 = vadd(g[1], g[3]), p24 = vadd(g[2], g[4]);
+    const T p56 = vadd(g[5], g[6]), p78 = vadd(g[7], g[8]);
+    const T d58 = vadd(p56, p78);
+    const T s10 = vadd(vadd(a13, a56), a87);
+    const T s01 = vadd(vsub(g[2], g[4]), vsub(p56, p78));
+    const T s20 = vadd(p13, d58);
+    const T s02 = vadd(p24, d58);
+    const T s11 = vsub(a56, a87);
+    const T s00 = vadd(vadd(g[0], d58), vadd(p13, p24));
 
     // hydrodynamic fields (rho u = sum f e + F / (2 gamma))
-    const T rho = T(1) + s00;
-    const T irho = rcp<T>(rho);
-    const T jx = s10 + k.hx;
-    const T jy = k.r * s01 + k.hy;
-    const T ux = jx * irho, uy = jy * irho;
-    const T ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const T rux2 = rho * ux2, ruy2 = rho * uy2, ruxy = rho * uxy;
+    const T rho = vadd(splat<T>(1.0), s00);
+    const T irho = vrcp(rho);
+    const T jx = FORCE ? vadd(s10, k.hx) : s10;
+    const T jy = FORCE ? vfma(k.r, s01, k.hy) : vmul(k.r, s01);
+    const T ux = vmul(jx, irho), uy = vmul(jy, irho);
+    const T ux2 = vmul(ux, ux), uy2 = vmul(uy, uy), uxy = vmul(ux, uy);
+    const T rux2 = vmul(jx, ux), ruy2 = vmul(jy, uy), ruxy = vmul(jx, uy);
+    const T sp = vadd(rux2, ruy2), sm = vsub(rux2, ruy2);
+    const T c2s00 = vmul(k.c2, s00);
 
     // non-equilibrium central moments w.r.t. the base equilibria of Eq. 14
-    const T n20 = s20 - k.c2 * s00 - k.ig * rux2 + T(2) * ux * k.hx;
-    const T n02 = k.r2 * s02 - k.c2 * s00 - k.ig * ruy2 + T(2) * uy * k.hy;
-    const T n11 = k.r * s11 - k.ig * ruxy + uy * k.hx + ux * k.hy;
-    const T n2s = n20 + n02, n2d = n20 - n02;
-
-    // local strain rates (Eqs. 43-48, R per Eq. 45)
-    T ebr = T(0), esr = T(0);
-    if (DRHO) {
-        const T A = k.Ax * ux, B = k.By * uy;
-        ebr = -A * dxr - B * dyr;
-        esr = -A * dxr + B * dyr;
+    T n2s = vfma(k.r2, s02, s20);
+    n2s = vfma(splat<T>(-2.0), c2s00, n2s);
+    n2s = vfma(k.nig, sp, n2s);
+    T n2d = vfma(k.nr2, s02, s20);
+    n2d = vfma(k.nig, sm, n2d);
+    T n11 = vfma(k.r, s11, vmul(k.nig, ruxy));
+    if (FORCE) {
+        const T fx2 = vmul(ux, k.hx), fy2 = vmul(uy, k.hy);
+        n2s = vfma(splat<T>(2.0), vadd(fx2, fy2), n2s);
+        n2d = vfma(splat<T>(2.0), vsub(fx2, fy2), n2d);
+        n11 = vfma(uy, k.hx, vfma(ux, k.hy, n11));
     }
-    const T R2s = n2s + ebr, R2d = n2d + esr;
-    const T Px = k.hPg * ux2, Py = k.hPg * uy2, Qx = k.hQg * ux2, Qy = k.hQg * uy2;
-    const T ax = (Px + Qy + k.k3x) * rho;
-    const T ay = (Py + Qx + k.k3y) * rho;
-    const T dx = (Px - Qy + k.k3x) * rho;
-    const T dy = (Py - Qx + k.k3y) * rho;
-    const T Cbx = k.Cb0 * rho + ax, Cby = k.Cb0 * rho + ay;
-    const T Csx = k.Cs0 * rho + dx, Csy = -k.Cs0 * rho - dy;
-    const T X = (Csy * R2s - Cby * R2d) * rcp<T>(Cbx * Csy - Csx * Cby);
-    const T Y = (R2s - Cbx * X) * rcp<T>(Cby);
 
-    // corrections of the extended equilibria (Eqs. 30, 38-40 / App. A)
-    const T corr_s = k.m2tau_xi * (ax * X + ay * Y - ebr);
-    const T corr_d = k.m2tau_nu * (dx * X - dy * Y - esr);
-    T c11 = k.Qg * ruxy * (X + Y);
-    if (DRHO) c11 += k.h1c2 * (uy * dxr + ux * dyr);
-    const T corr_11 = k.mtau_nu * c11;
+    // local strain rates (Eqs. 43-48, R per Eq. 45); nebr = -e_b,rho, nesr = -e_s,rho
+    T nebr = splat<T>(0.0), nesr = splat<T>(0.0);
+    if (DRHO) {
+        const T Adx = vmul(vmul(k.Ax, ux), dxr), Bdy = vmul(vmul(k.By, uy), dyr);
+        nebr = vadd(Adx, Bdy);
+        nesr = vsub(Adx, Bdy);
+    }
+    const T R2s = vsub(n2s, nebr), R2d = vsub(n2d, nesr);
+    const T ax = vmul(vfma(k.hPg, ux2, vfma(k.hQg, uy2, k.k3x)), rho);
+    const T ay = vmul(vfma(k.hPg, uy2, vfma(k.hQg, ux2, k.k3y)), rho);
+    const T dx = vmul(vfma(k.hPg, ux2, vfma(k.nhQg, uy2, k.k3x)), rho);
+    const T ndy = vmul(vfma(k.nhPg, uy2, vfma(k.hQg, ux2, k.nk3y)), rho);
+    const T Cb0r = vmul(k.Cb0, rho), Cs0r = vmul(k.Cs0, rho);
+    const T Cbx = vadd(Cb0r, ax), Cby = vadd(Cb0r, ay);
+    const T Csx = vadd(Cs0r, dx), Csy = vsub(ndy, Cs0r);
+    const T det = vsub(vmul(Cbx, Csy), vmul(Csx, Cby));
+    const T X = vmul(vsub(vmul(Csy, R2s), vmul(Cby, R2d)), vrcp(det));
+    const T Y = vmul(vsub(R2s, vmul(Cbx, X)), vrcp(Cby));
 
-    // central source moments (Eq. 13-central)
-    const T sig2s = k.twoQFx * ux + k.twoQFy * uy;
-    const T sig2d = k.twoQFx * ux - k.twoQFy * uy;
-    const T sig11 = k.QFx * uy + k.QFy * ux;
+    // extended-equilibrium corrections (Eqs. 30, 38-40 / App. A) and relaxation;
+    // hdt2s = (k~2s - 2 c^2 rho) / 2, ht2d = k~2d / 2
+    const T cs = vfma(ax, X, vfma(ay, Y, nebr));
+    const T cd = vfma(dx, X, vfma(ndy, Y, nesr));
+    T c11 = vmul(vmul(k.Qg, ruxy), vadd(X, Y));
+    if (DRHO) c11 = vfma(k.h1c2, vfma(uy, dxr, vmul(ux, dyr)), c11);
+    T hdt2s = vfma(k.hh1, sp, vfma(k.hxi, n2s, vmul(k.kxs, cs)));
+    T ht2d = vfma(k.hh1, sm, vfma(k.hnu, n2d, vmul(k.kd, cd)));
+    T t11 = vfma(k.h1, ruxy, vfma(k.one_m_w_nu, n11, vmul(k.kd, c11)));
+    if (FORCE) {
+        hdt2s = vfma(k.fsx, ux, vfma(k.fsy, uy, hdt2s));
+        ht2d = vfma(k.fdx, ux, vfma(k.nfdy, uy, ht2d));
+        t11 = vfma(k.fdx, uy, vfma(k.fdy, ux, t11));
+    }
+    const T dt20 = vadd(hdt2s, ht2d);  // k~20 - c^2 rho
+    const T dt02 = vsub(hdt2s, ht2d);  // k~02 - c^2 rho
+    const T c2rho = vmul(k.c2, rho);
+    const T t20 = vadd(c2rho, dt20), t02 = vadd(c2rho, dt02);
 
-    // relaxation (App. A); dt2s = k~2s - 2 c^2 rho
-    const T dt2s = k.h1 * (rux2 + ruy2) + k.one_m_w_xi * n2s + k.w_xi * corr_s + k.src_xi * sig2s;
-    const T t2d = k.h1 * (rux2 - ruy2) + k.one_m_w_nu * n2d + k.w_nu * corr_d + k.src_nu * sig2d;
-    const T t11 = k.h1 * ruxy + k.one_m_w_nu * n11 + k.w_nu * corr_11 + k.src_nu * sig11;
-    const T dt20 = T(0.5) * (dt2s + t2d);  // k~20 - c^2 rho
-    const T dt02 = T(0.5) * (dt2s - t2d);  // k~02 - c^2 rho
-    const T t21 = k.a3 * rux2 * uy;
-    const T t12 = k.a3 * ruy2 * ux;
-    const T t20 = k.c2 * rho + dt20, t02 = k.c2 * rho + dt02;
+    // post-collision raw moments minus the rest-state moments (F^-1), with
+    // k~21 = a3 rho u_x^2 u_y, k~12 = a3 rho u_x u_y^2, k~22 = c^4 rho
+    const T e21 = vmul(rux2, uy), e12 = vmul(ruy2, ux);
+    T D10 = jx, D01 = jy;
+    T D20 = vadd(vadd(c2s00, rux2), dt20);
+    T D02 = vadd(vadd(c2s00, ruy2), dt02);
+    T D11 = vadd(t11, ruxy);
+    T D21 = vfma(k.a3p1, e21, vfma(vadd(ux, ux), t11, vmul(uy, t20)));
+    T D12 = vfma(k.a3p1, e12, vfma(vadd(uy, uy), t11, vmul(ux, t02)));
+    T D22 = vfma(ux2, t02, vfma(uy2, t20, vfma(vmul(splat<T>(4.0), uxy), t11,
+                                                vfma(k.a34p1, vmul(e21, uy), vmul(k.c4, s00)))));
+    if (FORCE) {
+        const T hxuy = vmul(k.hx, uy), hyux = vmul(k.hy, ux);
+        D10 = vadd(D10, k.hx);
+        D01 = vadd(D01, k.hy);
+        D20 = vfma(vadd(ux, ux), k.hx, D20);
+        D02 = vfma(vadd(uy, uy), k.hy, D02);
+        D11 = vadd(D11, vadd(hxuy, hyux));
+        D21 = vfma(ux, vfma(splat<T>(2.0), hxuy, hyux), D21);
+        D12 = vfma(uy, vfma(splat<T>(2.0), hyux, hxuy), D12);
+        D22 = vfma(vadd(uxy, uxy), vadd(hxuy, hyux), D22);
+    }
 
-    // post-collision raw moments minus the rest-state moments (F^-1)
-    const T D00 = s00;
-    const T D10 = jx + k.hx;
-    const T D01 = jy + k.hy;
-    const T D20 = k.c2 * s00 + dt20 + T(2) * ux * k.hx + rux2;
-    const T D02 = k.c2 * s00 + dt02 + T(2) * uy * k.hy + ruy2;
-    const T D11 = t11 + uy * k.hx + ux * k.hy + ruxy;
-    const T D21 = t21 + T(2) * ux * t11 + ux2 * k.hy + uy * t20 + T(2) * uxy * k.hx + rux2 * uy;
-    const T D12 = t12 + T(2) * uy * t11 + uy2 * k.hx + ux * t02 + T(2) * uxy * k.hy + ruy2 * ux;
-    const T D22 = k.c4 * s00 + T(2) * ux * t12 + ux2 * t02 + T(2) * uy * t21 + T(4) * uxy * t11
-                + T(2) * ux2 * uy * k.hy + uy2 * t20 + T(2) * ux * uy2 * k.hx + rux2 * uy2;
-
-    // S^-1 then P^-1 (Eq. 72)
-    const T e01 = D01 * k.inv_r, e02 = D02 * k.inv_r2, e11 = D11 * k.inv_r;
-    const T e21 = D21 * k.inv_r, e12 = D12 * k.inv_r2, e22 = D22 * k.inv_r2;
-    g[0] = (D00 - D20) + (e22 - e02);
-    const T a1 = T(0.5) * (D20 - e22), b1 = T(0.5) * (D10 - e12);
-    g[1] = a1 + b1;
-    g[3] = a1 - b1;
-    const T a2 = T(0.5) * (e02 - e22), b2 = T(0.5) * (e01 - e21);
-    g[2] = a2 + b2;
-    g[4] = a2 - b2;
-    const T p = T(0.25) * (e21 + e22), m = T(0.25) * (e11 + e12);
-    const T pp = T(0.25) * (e22 - e21), mm = T(0.25) * (e11 - e12);
-    g[5] = p + m;
-    g[6] = p - m;
-    g[7] = pp + mm;
-    g[8] = pp - mm;
+    // S^-1 then P^-1 (Eq. 72) with the 1/2, 1/4 and 1/r^n factors folded
+    const T Q11 = vmul(D11, k.qr), Q21 = vmul(D21, k.qr), Q12 = vmul(D12, k.qr2), Q22 = vmul(D22, k.qr2);
+    const T p = vadd(Q21, Q22), m = vadd(Q11, Q12), pp = vsub(Q22, Q21), mm = vsub(Q11, Q12);
+    g[5] = vadd(p, m);
+    g[6] = vsub(p, m);
+    g[7] = vadd(pp, mm);
+    g[8] = vsub(pp, mm);
+    const T n2Q22 = vmul(splat<T>(-2.0), Q22);
+    const T a1 = vfma(splat<T>(0.5), D20, n2Q22);
+    const T b1 = vfma(splat<T>(0.5), D10, vmul(splat<T>(-2.0), Q12));
+    g[1] = vadd(a1, b1);
+    g[3] = vsub(a1, b1);
+    const T a2 = vfma(k.hr2, D02, n2Q22);
+    const T b2 = vfma(k.hr, D01, vmul(splat<T>(-2.0), Q21));
+    g[2] = vadd(a2, b2);
+    g[4] = vsub(a2, b2);
+    g[0] = vfma(splat<T>(4.0), Q22, vfma(k.ninv_r2, D02, vsub(s00, D20)));
 
     ux_out = ux;
     uy_out = uy;

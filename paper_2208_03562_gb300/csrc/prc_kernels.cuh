@@ -26,7 +26,7 @@ struct Rects {
 // EPI the step also accumulates (u_x - u_x,snapshot)^2 and drho per CTA for the
 // residual of Sec. 5.2 and refreshes the snapshot; the CTA totals go to
 // partials[part0 + blockIdx.x].
-template <typename S, typename T, bool DRHO, bool EPI>
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(BX * BY)
 k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
        double2 *__restrict__ partials, const DevStatus *__restrict__ st, Rects rc, int part0)
@@ -74,7 +74,7 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
 
     T ux = T(0), uy = T(0), drho = T(0);
     if (valid) {
-        collide<T, DRHO>(k, g, dxr, dyr, ux, uy, drho);
+        collide<T, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
         const long long o = (long long)y * gd.pitch + x;
 #pragma unroll
         for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>(g[i]);
@@ -113,8 +113,9 @@ __global__ void k_init_fields(S *__restrict__ dst, Grid gd, Coef<double> k, doub
     const double D21 = rho * (k.c2 + ux * ux * ig * ig) * uy;
     const double D12 = rho * (k.c2 + uy * uy * ig * ig) * ux;
     const double D22 = k.c4 * drho + rho * k.c2 * (ux * ux + uy * uy) + rho * ux * ux * uy * uy;
-    const double e01 = D01 * k.inv_r, e02 = D02 * k.inv_r2, e11 = D11 * k.inv_r;
-    const double e21 = D21 * k.inv_r, e12 = D12 * k.inv_r2, e22 = D22 * k.inv_r2;
+    const double ir = 1.0 / k.r;
+    const double e01 = D01 * ir, e02 = D02 * k.inv_r2, e11 = D11 * ir;
+    const double e21 = D21 * ir, e12 = D12 * k.inv_r2, e22 = D22 * k.inv_r2;
     double g[9];
     g[0] = D00 - D20 - e02 + e22;
     g[1] = 0.5 * (D10 + D20 - e12 - e22);

@@ -17,7 +17,7 @@ inline Coef<T> cast_coef(const Coef<double> &d)
     Coef<T> c;
     const double *s = reinterpret_cast<const double *>(&d);
     T *o = reinterpret_cast<T *>(&c);
-    for (size_t i = 0; i < sizeof(Coef<double>) / sizeof(double); i++) o[i] = (T)s[i];
+    for (size_t i = 0; i < sizeof(Coef<double>) / sizeof(double); i++) o[i] = from_double<T>(s[i]);
     return c;
 }
 
@@ -41,7 +41,7 @@ struct DtypeOps {
     cudaError_t (*prepare)();
     cudaError_t (*step)(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
                         const Coef<double> &k, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
-                        cudaStream_t s);
+                        bool force, cudaStream_t s);
     cudaError_t (*init_fields)(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
                                const double *ux, const double *uy, void *snap, cudaStream_t s);
     cudaError_t (*fields)(const void *src, const Grid &gd, const Coef<double> &k, double *rho, double *ux,

@@ -12,72 +12,90 @@ using S = PRC_S;
 using T = PRC_T;
 constexpr int TW = PRC_TMA_W, TH = PRC_TMA_H;
 
-template <bool DRHO, bool EPI>
-cudaError_t launch_tma(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn,
+template <bool DRHO, bool EPI, bool FORCE>
+cudaError_t launch_tma(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<F2> &k, float *sn,
                        double2 *partials, DevStatus *st, cudaStream_t s)
 {
     if constexpr (TW > 0) {
         using Cf = TmaCfg<S, TW, TH>;
-        k_step_tma<S, T, TW, TH, DRHO, EPI><<<pl.n_int_ctas, Cf::THREADS, Cf::SMEM, s>>>(*tsrc, b, gd, k, sn,
-                                                                                        partials, st, pl.in);
+        k_step_tma<S, TW, TH, DRHO, EPI, FORCE><<<pl.n_int_ctas, Cf::THREADS, Cf::SMEM, s>>>(*tsrc, b, gd, k, sn,
+                                                                                            partials, st, pl.in);
         return cudaGetLastError();
     } else {
         return cudaErrorNotSupported;
     }
 }
 
-// opt the interior kernels into their dynamic shared memory (once, outside
-// any stream capture)
-cudaError_t op_prepare()
+template <bool DRHO, bool EPI, bool FORCE>
+cudaError_t set_smem_attr()
 {
     if constexpr (TW > 0) {
-        using Cf = TmaCfg<S, TW, TH>;
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, false, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, false, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, true, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM)) != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_step_tma<S, T, TW, TH, true, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM);
+        return cudaFuncSetAttribute(k_step_tma<S, TW, TH, DRHO, EPI, FORCE>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TmaCfg<S, TW, TH>::SMEM);
     }
     return cudaSuccess;
 }
 
-template <bool DRHO, bool EPI>
+// opt the interior kernels into their dynamic shared memory (once, outside
+// any stream capture)
+cudaError_t op_prepare()
+{
+    cudaError_t e;
+    if ((e = set_smem_attr<false, false, false>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<false, true, false>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<true, false, false>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<true, true, false>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<false, false, true>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<false, true, true>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<true, false, true>()) != cudaSuccess) return e;
+    return set_smem_attr<true, true, true>();
+}
+
+template <bool DRHO, bool EPI, bool FORCE>
 cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn,
                            double2 *partials, const DevStatus *st, cudaStream_t s)
 {
-    k_step<S, T, DRHO, EPI><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st, pl.edge,
-                                                                    pl.n_int_ctas);
+    k_step<S, T, DRHO, EPI, FORCE><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st, pl.edge,
+                                                                           pl.n_int_ctas);
     return cudaGetLastError();
 }
 
-template <bool DRHO, bool EPI>
+template <bool DRHO, bool EPI, bool FORCE>
 cudaError_t step_both(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
-                      const Coef<T> &k, T *sn, double2 *partials, DevStatus *st, cudaStream_t s)
+                      const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    if (pl.tma) e = launch_tma<DRHO, EPI>(tsrc, static_cast<S *>(dst), pl, gd, k, sn, partials, st, s);
+    if (pl.tma) {
+        if constexpr (TW > 0)
+            e = launch_tma<DRHO, EPI, FORCE>(tsrc, static_cast<S *>(dst), pl, gd, cast_coef<F2>(kd),
+                                             static_cast<float *>(snap), partials, st, s);
+        else
+            e = cudaErrorNotSupported;
+    }
     if (e == cudaSuccess && pl.n_edge_ctas > 0)
-        e = launch_general<DRHO, EPI>(static_cast<const S *>(src), static_cast<S *>(dst), pl, gd, k, sn, partials,
-                                      st, s);
+        e = launch_general<DRHO, EPI, FORCE>(static_cast<const S *>(src), static_cast<S *>(dst), pl, gd,
+                                             cast_coef<T>(kd), static_cast<T *>(snap), partials, st, s);
     return e;
+}
+
+template <bool DRHO, bool EPI>
+cudaError_t step_f(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
+                   const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool force, cudaStream_t s)
+{
+    if (force) return step_both<DRHO, EPI, true>(src, dst, tsrc, pl, gd, kd, snap, partials, st, s);
+    return step_both<DRHO, EPI, false>(src, dst, tsrc, pl, gd, kd, snap, partials, st, s);
 }
 
 cudaError_t op_step(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
                     const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
-                    cudaStream_t s)
+                    bool force, cudaStream_t s)
 {
-    const Coef<T> k = cast_coef<T>(kd);
-    T *sn = static_cast<T *>(snap);
     if (drho) {
-        if (epi) return step_both<true, true>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
-        return step_both<true, false>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
+        if (epi) return step_f<true, true>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
+        return step_f<true, false>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
     }
-    if (epi) return step_both<false, true>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
-    return step_both<false, false>(src, dst, tsrc, pl, gd, k, sn, partials, st, s);
+    if (epi) return step_f<false, true>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
+    return step_f<false, false>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
 }
 
 dim3 row_grid(const Grid &gd) { return dim3((gd.nx + 127) / 128, gd.ny, 1); }

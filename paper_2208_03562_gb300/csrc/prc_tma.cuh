@@ -88,16 +88,55 @@ struct TmaCfg {
     static constexpr int BOX_BYTES = BW * BH * (int)sizeof(S);
     static constexpr int PLANE_BYTES = (BOX_BYTES + 127) / 128 * 128;
     static constexpr int STAGE_BYTES = 9 * PLANE_BYTES;
-    static constexpr int RW = W + 2, RH = H + 2;      // density tile with ring
+    static constexpr int RW = W + 4, RH = H + 2;      // density tile: node lx at column lx + 2
     static constexpr int R_BYTES = (RW * RH * 4 + 127) / 128 * 128;
     static constexpr int SMEM = 2 * STAGE_BYTES + R_BYTES + 128 + 128;  // + barriers, + base alignment
     static constexpr int THREADS = 512;
+    static constexpr int PAIRS = W / 2;               // node pairs per tile row
 };
 
-template <typename S, typename T, int W, int H, bool DRHO, bool EPI>
+// Shared-memory access to a pair of neighbouring nodes (x, x+1) of one plane.
+template <typename S>
+struct Pair;
+template <>
+struct Pair<float> {
+    static __device__ __forceinline__ F2 aligned(const float *p) { return F2(*reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ F2 any(const float *p) { return F2(p[0], p[1]); }
+    static __device__ __forceinline__ float one(const float *p) { return *p; }
+    static __device__ __forceinline__ void store(float *p, F2 v) { *reinterpret_cast<float2 *>(p) = v.v; }
+};
+template <>
+struct Pair<__half> {
+    static __device__ __forceinline__ F2 aligned(const __half *p)
+    {
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p)));
+    }
+    static __device__ __forceinline__ F2 any(const __half *p) { return F2(__half2float(p[0]), __half2float(p[1])); }
+    static __device__ __forceinline__ float one(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void store(__half *p, F2 v)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.v.x, v.v.y);
+    }
+};
+
+// The nine pulled values of the node pair whose first node sits at element
+// `b` of plane 0 (ring-relative addressing: pull from plane i at b + i PE - e_ix).
+template <typename S, int PE>
+__device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        if (ex_of(i) == 0) g[i] = Pair<S>::aligned(b + i * PE);
+        else g[i] = Pair<S>::any(b + i * PE - ex_of(i));
+    }
+}
+
+// Persistent interior kernel: two neighbouring nodes per thread, collision in
+// packed FP32x2 arithmetic.
+template <typename S, int W, int H, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(512, 1)
-k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid gd, Coef<T> k,
-           T *__restrict__ snap, double2 *__restrict__ partials, DevStatus *__restrict__ st, Interior in)
+k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid gd, Coef<F2> k,
+           float *__restrict__ snap, double2 *__restrict__ partials, DevStatus *__restrict__ st, Interior in)
 {
     using C = TmaCfg<S, W, H>;
     if (st->stop) return;
@@ -132,14 +171,14 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
         for (int i = 0; i < 9; i++) tma_load_3d(stg + i * PE, &tsrc, b, x0 - C::PADX, y0 - 1 - ey_of(i), i);
     };
 
-    RedAcc<T> acc;
+    RedAcc<float> acc;
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) issue(tile, stage0, &bar[0]);
     bool in_flight_other = false;  // (thread 0) a copy into the other stage is outstanding
     int it = 0;
     for (; tile < ntiles; it++, tile += gridDim.x) {
         const int s = it & 1;
-        S *cur = s ? stage1 : stage0;
+        const S *cur = s ? stage1 : stage0;
         const int next = tile + gridDim.x;
         if (tid == 0) {
             in_flight_other = next < ntiles;
@@ -159,42 +198,60 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
         origin(tile, x0, y0, ox, oy);
 
         if constexpr (DRHO) {
-            // density (minus rho0) of the tile and its ring
-            for (int q = tid; q < C::RW * C::RH; q += C::THREADS) {
-                const int ly = q / C::RW, lx = q - ly * C::RW;  // ly, lx offset by +1
-                const S *b = cur + ly * C::BW + lx - 1 + C::PADX;
-                T sum = T(0);
+            // density (minus rho0) of the tile rows and the ring rows, by pairs
+            for (int q = tid; q < C::RH * C::PAIRS; q += C::THREADS) {
+                const int ry = q / C::PAIRS, x = 2 * (q - ry * C::PAIRS);  // ry = ly + 1
+                F2 g[9];
+                pull_pair<S, PE>(cur + ry * C::BW + x + C::PADX, g);
+                *reinterpret_cast<float2 *>(R + ry * C::RW + x + 2) = sum9(g).v;
+            }
+            // ring columns lx = -1 and lx = W
+            for (int q = tid; q < 2 * C::RH; q += C::THREADS) {
+                const int ry = q >> 1, lx = (q & 1) ? W : -1;
+                const S *b = cur + ry * C::BW + lx + C::PADX;
+                float sum = 0.f;
 #pragma unroll
-                for (int i = 0; i < 9; i++) sum += ld_smem<S, T>(b + i * PE - ex_of(i));
-                R[q] = (float)sum;
+                for (int i = 0; i < 9; i++) sum += Pair<S>::one(b + i * PE - ex_of(i));
+                R[ry * C::RW + lx + 2] = sum;
             }
             __syncthreads();
         }
 
-        for (int q = tid; q < W * H; q += C::THREADS) {
-            const int ly = q / W, lx = q - ly * W;
-            const S *b = cur + (ly + 1) * C::BW + lx + C::PADX;
-            T g[9];
-#pragma unroll
-            for (int i = 0; i < 9; i++) g[i] = ld_smem<S, T>(b + i * PE - ex_of(i));
-            T dxr = T(0), dyr = T(0);
+        for (int q = tid; q < H * C::PAIRS; q += C::THREADS) {
+            const int ly = q / C::PAIRS, x = 2 * (q - ly * C::PAIRS);
+            F2 g[9];
+            pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
+            F2 dxr(0.f), dyr(0.f);
             if constexpr (DRHO) {
-                const float *c = R + (ly + 1) * C::RW + (lx + 1);
-                const T rE = c[1], rW = c[-1], rN = c[C::RW], rS = c[-C::RW];
-                const T rNE = c[C::RW + 1], rNW = c[C::RW - 1], rSE = c[-C::RW + 1], rSW = c[-C::RW - 1];
-                dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
-                dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+                const float *c = R + (ly + 1) * C::RW + x + 2;
+                const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
+                             Rr = *reinterpret_cast<const float2 *>(c + 2);
+                const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
+                             NM = *reinterpret_cast<const float2 *>(c + C::RW),
+                             NR = *reinterpret_cast<const float2 *>(c + C::RW + 2);
+                const float2 SL = *reinterpret_cast<const float2 *>(c - C::RW - 2),
+                             SM = *reinterpret_cast<const float2 *>(c - C::RW),
+                             SR = *reinterpret_cast<const float2 *>(c - C::RW + 2);
+                const float i12 = k.inv12.v.x, i12r = k.inv12r.v.x;
+                // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
+                // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
+                dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
+                         (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
+                dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
+                         (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
             }
-            T ux, uy, drho;
-            collide<T, DRHO>(k, g, dxr, dyr, ux, uy, drho);
-            const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + lx);
+            F2 ux, uy, drho;
+            collide<F2, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
+            const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
 #pragma unroll
-            for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>(g[i]);
+            for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[i]);
             if constexpr (EPI) {
-                if (x0 + lx >= ox && y0 + ly >= oy) {
-                    const T d = ux - snap[o];
-                    snap[o] = ux;
-                    acc.add(d * d, drho);
+                if (x0 + x >= ox && y0 + ly >= oy) {  // the pair is owned by this tile
+                    const float2 sn = *reinterpret_cast<const float2 *>(snap + o);
+                    *reinterpret_cast<float2 *>(snap + o) = ux.v;
+                    const float da = ux.v.x - sn.x, db = ux.v.y - sn.y;
+                    acc.add(da * da, drho.v.x);
+                    acc.add(db * db, drho.v.y);
                 }
             }
         }
