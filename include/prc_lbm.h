@@ -207,6 +207,25 @@ lbm_status lbm_save_bytes(lbm_t h, size_t *bytes);
 lbm_status lbm_save(lbm_t h, void *host_buf, size_t n);
 lbm_status lbm_load(lbm_t h, const void *host_buf, size_t n);
 
+/*
+ * Interior-kernel variants.  Nodes at least two lattice spacings from every
+ * wall are updated by a TMA-staged persistent kernel compiled in a few tile
+ * shapes; the rest by the general wall-aware kernel.  These calls list the
+ * compiled variants of a storage type, select one for a handle (-1 = the
+ * general kernel everywhere; results agree to round-off), and time every
+ * variant on the handle's own grid.  lbm_autotune runs `steps` plain steps
+ * per variant (rounded up to even), then restores the populations, the
+ * residual snapshot, the status and the step counter exactly, selects the
+ * fastest variant and returns its index in *best and the per-variant
+ * milliseconds per step in ms_per_step[0..n) (either may be NULL).
+ * No counterpart in the paper: these choose how the same update is executed.
+ */
+lbm_status lbm_variant_count(int dtype, int *n);
+lbm_status lbm_variant_info(int dtype, int variant, int *tile_w, int *tile_h, int *threads, int *ctas_per_sm);
+lbm_status lbm_get_variant(lbm_t h, int *variant);
+lbm_status lbm_set_variant(lbm_t h, int variant);
+lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step);
+
 /* Derived constants: shear relaxation rate omega_nu and q = min(1, r). */
 lbm_status lbm_omega_nu(const lbm_params *p, double *omega_nu);
 

@@ -3,7 +3,6 @@
 // device-side stop rule of lbm_run, residual/mass finalisation, field and
 // population transfers, checkpoints.
 #include <cmath>
-#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -56,14 +55,16 @@ void add_rect(prc::Rects &rc, int x0, int y0, int x1, int y1)
 // from every wall, x origin 16-byte aligned) and the general kernel on the
 // remaining edge strips.  num_sms <= 0 gives the upper bound used to size the
 // workspace.
-Plan make_plan(const lbm_params &p, int num_sms)
+Plan make_plan(const lbm_params &p, int num_sms, int variant)
 {
     const prc::DtypeOps *ops = ops_for(p.dtype);
     Plan pl;
     std::memset(&pl, 0, sizeof(pl));
-    const int W = ops->tma_w, H = ops->tma_h, PX = ops->tma_padx;
+    const bool have = variant >= 0 && variant < ops->nvariants;
+    const int W = have ? ops->variants[variant].w : 0, H = have ? ops->variants[variant].h : 0;
+    const int PX = ops->tma_padx;
     const int ix0 = PX, iy0 = 2;
-    if (W > 0 && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
+    if (have && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
         const int xlast = ((p.nx - 2 - W) / PX) * PX;
         const int ylast = p.ny - 2 - H;
         const int xend = xlast + W, yend = ylast + H;
@@ -76,7 +77,8 @@ Plan make_plan(const lbm_params &p, int num_sms)
         pl.in.ylast = ylast;
         const int ntiles = pl.in.ntx * pl.in.nty;
         int g = ntiles < prc::MAX_INTERIOR_CTAS ? ntiles : prc::MAX_INTERIOR_CTAS;
-        if (num_sms > 0 && g > num_sms) g = num_sms;
+        const int resident = num_sms * ops->variants[variant].ctas_per_sm;
+        if (num_sms > 0 && g > resident) g = resident;
         pl.n_int_ctas = g;
         add_rect(pl.edge, 0, 0, p.nx, iy0);
         add_rect(pl.edge, 0, yend, p.nx, p.ny);
@@ -105,9 +107,12 @@ Layout make_layout(const lbm_params &p)
     L.plane = (size_t)L.pitch * (size_t)p.ny;
     L.pop_bytes = align_up(9 * L.plane * ops->elem, ALIGN);
     L.snap_bytes = align_up(L.plane * ops->snap_elem, ALIGN);
-    const int mass_parts = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
-    const int step_parts = make_plan(p, 0).nparts;
-    L.nparts = mass_parts > step_parts ? mass_parts : step_parts;
+    int np = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);  // mass reduction
+    for (int v = -1; v < ops->nvariants; v++) {
+        const int n = make_plan(p, 0, v).nparts;
+        if (n > np) np = n;
+    }
+    L.nparts = np;
     L.part_bytes = align_up((size_t)L.nparts * sizeof(double2), ALIGN);
     L.st_bytes = align_up(sizeof(DevStatus), ALIGN);
     L.off_pop0 = 0;
@@ -297,6 +302,8 @@ struct lbm_s {
     DevStatus *st_host;  // pinned mirror
     long long t;         // completed steps; invariant: the state is in pop[t & 1]
     Plan plan;
+    int variant;          // interior-kernel variant (-1: general kernel only)
+    int num_sms;
     CUtensorMap tmap[2];  // TMA descriptors of the two population sets
     cudaGraphExec_t g20;
     bool have_g20;
@@ -338,9 +345,13 @@ lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
 {
     const bool epi = ((t_before + 1) % RES_INTERVAL) == 0;
     const int c = (int)(t_before & 1);
-    CK(h, h->ops->step(h->pop[c], h->pop[c ^ 1], h->plan.tma ? &h->tmap[c] : nullptr, h->plan, h->gd, h->k,
-                       h->snap, h->partials, h->st, h->p.drho == LBM_DRHO_CURRENT, epi,
-                       h->p.fx != 0.0 || h->p.fy != 0.0, s));
+    const bool drho = h->p.drho == LBM_DRHO_CURRENT, force = h->p.fx != 0.0 || h->p.fy != 0.0;
+    if (h->plan.tma)
+        CK(h, h->ops->variants[h->variant].launch(&h->tmap[c], h->pop[c ^ 1], h->plan, h->gd, h->k, h->snap,
+                                                   h->partials, h->st, drho, epi, force, s));
+    if (h->plan.n_edge_ctas > 0)
+        CK(h, h->ops->step_general(h->pop[c], h->pop[c ^ 1], h->plan, h->gd, h->k, h->snap, h->partials, h->st,
+                                   drho, epi, force, s));
     if (epi) {
         k_finalize<<<1, 256, 0, s>>>(h->partials, h->plan.nparts, h->st, (double)h->p.nx * (double)h->p.ny);
         CK(h, cudaGetLastError());
@@ -442,13 +453,33 @@ lbm_status make_tmaps(lbm_t h)
                                  : (elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
     const cuuint64_t dims[3] = {(cuuint64_t)h->p.nx, (cuuint64_t)h->p.ny, 9};
     const cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * elem, (cuuint64_t)h->L.plane * elem};
-    const cuuint32_t box[3] = {(cuuint32_t)(h->ops->tma_w + 2 * h->ops->tma_padx), (cuuint32_t)(h->ops->tma_h + 2), 1};
+    const prc::Variant &v = h->ops->variants[h->variant];
+    const cuuint32_t box[3] = {(cuuint32_t)(v.w + 2 * h->ops->tma_padx), (cuuint32_t)(v.h + 2), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     for (int b = 0; b < 2; b++) {
         CUresult r = encode(&h->tmap[b], dt, 3, h->pop[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    }
+    return LBM_OK;
+}
+
+// Select the interior-kernel variant (-1: general kernel everywhere): plan,
+// TMA descriptors, shared-memory opt-in; drops the captured graph.
+lbm_status apply_variant(lbm_t h, int variant)
+{
+    if (variant < -1 || variant >= h->ops->nvariants) return fail(h, LBM_EINVAL, "no such variant");
+    h->variant = variant;
+    h->plan = make_plan(h->p, h->num_sms, variant);
+    if (h->plan.tma) {
+        lbm_status ts = make_tmaps(h);
+        if (ts != LBM_OK) return ts;
+        CK(h, h->ops->variants[variant].prepare());
+    }
+    if (h->have_g20) {
+        cudaGraphExecDestroy(h->g20);
+        h->have_g20 = false;
     }
     return LBM_OK;
 }
@@ -473,23 +504,9 @@ lbm_status init_handle(lbm_t h, const lbm_params &p, void *ws, size_t ws_bytes, 
     h->st = reinterpret_cast<DevStatus *>(h->ws + h->L.off_st);
     h->t = 0;
     h->have_g20 = false;
-    int nsm = 0;
-    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    h->plan = make_plan(p, nsm);
-    // PRC_LBM_GENERAL_ONLY=1 runs every node through the general kernel (for
-    // comparing the two code paths)
-    const char *gen = std::getenv("PRC_LBM_GENERAL_ONLY");
-    if (gen && gen[0] == '1') {
-        lbm_params q = p;
-        q.dtype = LBM_F64;  // the FP64 table has no interior tile
-        Plan g = make_plan(q, nsm);
-        h->plan = g;
-    }
-    if (h->plan.tma) {
-        lbm_status ts = make_tmaps(h);
-        if (ts != LBM_OK) return ts;
-        CK(h, h->ops->prepare());
-    }
+    CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    lbm_status vs = apply_variant(h, h->ops->nvariants > 0 ? 0 : -1);
+    if (vs != LBM_OK) return vs;
     CK(h, cudaMallocHost(&h->st_host, sizeof(DevStatus)));
     // rest state f~ = w(r): zero shifted storage everywhere (padding too)
     CK(h, cudaMemsetAsync(h->ws, 0, h->L.off_part, h->stream));
@@ -857,6 +874,109 @@ lbm_status lbm_get_populations(lbm_t h, double *f, int on_device)
     CK(h, cudaMemcpyAsync(f, tmp.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
+}
+
+lbm_status lbm_variant_count(int dtype, int *n)
+{
+    const prc::DtypeOps *ops = ops_for(dtype);
+    if (!ops || !n) return fail(nullptr, LBM_EINVAL, "bad dtype / null out");
+    *n = ops->nvariants;
+    return LBM_OK;
+}
+
+lbm_status lbm_variant_info(int dtype, int variant, int *tile_w, int *tile_h, int *threads, int *ctas_per_sm)
+{
+    const prc::DtypeOps *ops = ops_for(dtype);
+    if (!ops || variant < 0 || variant >= ops->nvariants) return fail(nullptr, LBM_EINVAL, "no such variant");
+    const prc::Variant &v = ops->variants[variant];
+    if (tile_w) *tile_w = v.w;
+    if (tile_h) *tile_h = v.h;
+    if (threads) *threads = v.threads;
+    if (ctas_per_sm) *ctas_per_sm = v.ctas_per_sm;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_variant(lbm_t h, int *variant)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (!variant) return fail(h, LBM_EINVAL, "null out");
+    *variant = h->variant;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_variant(lbm_t h, int variant)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return apply_variant(h, variant);
+}
+
+lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
+{
+    lbm_status s = enter(h);
+    if (s != LBM_OK) return s;
+    if (steps < 2) return fail(h, LBM_EINVAL, "autotune needs >= 2 steps");
+    steps += steps & 1;  // even: the state returns to its buffer
+    const int nv = h->ops->nvariants;
+    if (nv == 0) {
+        if (best) *best = -1;
+        return LBM_OK;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    // keep the state: copy the current populations, snapshot and status aside
+    const long long t_keep = h->t;
+    void *keep = nullptr;
+    const size_t kb = h->L.pop_bytes + h->L.snap_bytes + sizeof(DevStatus);
+    CK(h, cudaMallocAsync(&keep, kb, h->stream));
+    char *kc = static_cast<char *>(keep);
+    CK(h, cudaMemcpyAsync(kc, cur_pop(h), h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(kc + h->L.pop_bytes, h->snap, h->L.snap_bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(kc + h->L.pop_bytes + h->L.snap_bytes, h->st, sizeof(DevStatus), cudaMemcpyDeviceToDevice,
+                          h->stream));
+    k_status_arm<<<1, 1, 0, h->stream>>>(h->st, -1.0);
+    CK(h, cudaGetLastError());
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    int arg = -1;
+    double bestms = 1e300;
+    lbm_status rs = LBM_OK;
+    for (int v = 0; v < nv && rs == LBM_OK; v++) {
+        rs = apply_variant(h, v);
+        if (rs != LBM_OK) break;
+        // plain steps only: a step index of 0 or 1 (same buffer parity as t)
+        // never carries the residual epilogue
+        const long long t0 = h->t;
+        for (int i = 0; i < 2 && rs == LBM_OK; i++) rs = launch_one(h, h->stream, h->t & 1), h->t++;  // warm
+        cudaEventRecord(e0, h->stream);
+        for (int i = 0; i < steps && rs == LBM_OK; i++) rs = launch_one(h, h->stream, h->t & 1), h->t++;
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / steps;
+        if (ms_per_step) ms_per_step[v] = per;
+        if (per < bestms) {
+            bestms = per;
+            arg = v;
+        }
+        h->t = t0;  // even number of launches: the state is back in pop[t & 1]
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the state
+    h->t = t_keep;
+    cudaMemcpyAsync(cur_pop(h), kc, h->L.pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->snap, kc + h->L.pop_bytes, h->L.snap_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->st, kc + h->L.pop_bytes + h->L.snap_bytes, sizeof(DevStatus), cudaMemcpyDeviceToDevice,
+                    h->stream);
+    cudaFreeAsync(keep, h->stream);
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (rs != LBM_OK) return rs;
+    if (best) *best = arg;
+    return apply_variant(h, arg);
 }
 
 namespace {

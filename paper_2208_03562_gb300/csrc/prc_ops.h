@@ -33,15 +33,29 @@ struct Plan {
 };
 
 constexpr int MAX_INTERIOR_CTAS = 1024;
+constexpr int MAX_VARIANTS = 4;
+
+// One compiled configuration of the interior kernel.
+struct Variant {
+    int w, h;         // tile (nodes)
+    int threads;      // CTA size
+    int ctas_per_sm;  // resident CTAs per SM (shared memory / register budget)
+    cudaError_t (*prepare)();
+    cudaError_t (*launch)(const CUtensorMap *tsrc, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &k,
+                          void *snap, double2 *partials, DevStatus *st, bool drho, bool epi, bool force,
+                          cudaStream_t s);
+};
 
 struct DtypeOps {
     size_t elem;       // bytes per stored population
     size_t snap_elem;  // bytes per snapshot value (collision precision)
-    int tma_w, tma_h, tma_padx;  // interior tile (0: no TMA path)
-    cudaError_t (*prepare)();
-    cudaError_t (*step)(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
-                        const Coef<double> &k, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
-                        bool force, cudaStream_t s);
+    int tma_padx;      // 16-byte alignment of the TMA x origin, in elements
+    int nvariants;     // interior-kernel variants (0: general kernel only)
+    Variant variants[MAX_VARIANTS];
+    // general kernel on the rectangles of the plan (edge strips)
+    cudaError_t (*step_general)(const void *src, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &k,
+                                void *snap, double2 *partials, const DevStatus *st, bool drho, bool epi, bool force,
+                                cudaStream_t s);
     cudaError_t (*init_fields)(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
                                const double *ux, const double *uy, void *snap, cudaStream_t s);
     cudaError_t (*fields)(const void *src, const Grid &gd, const Coef<double> &k, double *rho, double *ux,

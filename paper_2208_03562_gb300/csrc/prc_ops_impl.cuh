@@ -10,45 +10,61 @@ namespace {
 
 using S = PRC_S;
 using T = PRC_T;
-constexpr int TW = PRC_TMA_W, TH = PRC_TMA_H;
 
-template <bool DRHO, bool EPI, bool FORCE>
-cudaError_t launch_tma(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<F2> &k, float *sn,
-                       double2 *partials, DevStatus *st, cudaStream_t s)
+template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
+cudaError_t launch_tma_t(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<F2> &k,
+                         float *sn, double2 *partials, DevStatus *st, cudaStream_t s)
 {
-    if constexpr (TW > 0) {
-        using Cf = TmaCfg<S, TW, TH>;
-        k_step_tma<S, TW, TH, DRHO, EPI, FORCE><<<pl.n_int_ctas, Cf::THREADS, Cf::SMEM, s>>>(*tsrc, b, gd, k, sn,
-                                                                                            partials, st, pl.in);
-        return cudaGetLastError();
-    } else {
-        return cudaErrorNotSupported;
-    }
+    using Cf = TmaCfg<S, W, H, THREADS>;
+    k_step_tma<S, W, H, THREADS, MINB, DRHO, EPI, FORCE><<<pl.n_int_ctas, THREADS, Cf::SMEM, s>>>(
+        *tsrc, b, gd, k, sn, partials, st, pl.in);
+    return cudaGetLastError();
 }
 
-template <bool DRHO, bool EPI, bool FORCE>
-cudaError_t set_smem_attr()
+template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI>
+cudaError_t launch_tma_f(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<F2> &k,
+                         float *sn, double2 *partials, DevStatus *st, bool force, cudaStream_t s)
 {
-    if constexpr (TW > 0) {
-        return cudaFuncSetAttribute(k_step_tma<S, TW, TH, DRHO, EPI, FORCE>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TmaCfg<S, TW, TH>::SMEM);
-    }
-    return cudaSuccess;
+    if (force) return launch_tma_t<W, H, THREADS, MINB, DRHO, EPI, true>(tsrc, b, pl, gd, k, sn, partials, st, s);
+    return launch_tma_t<W, H, THREADS, MINB, DRHO, EPI, false>(tsrc, b, pl, gd, k, sn, partials, st, s);
 }
 
-// opt the interior kernels into their dynamic shared memory (once, outside
-// any stream capture)
-cudaError_t op_prepare()
+template <int W, int H, int THREADS, int MINB>
+cudaError_t launch_tma(const CUtensorMap *tsrc, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &kd,
+                       void *snap, double2 *partials, DevStatus *st, bool drho, bool epi, bool force, cudaStream_t s)
+{
+    const Coef<F2> k = cast_coef<F2>(kd);
+    S *b = static_cast<S *>(dst);
+    float *sn = static_cast<float *>(snap);
+    if (drho) {
+        if (epi) return launch_tma_f<W, H, THREADS, MINB, true, true>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
+        return launch_tma_f<W, H, THREADS, MINB, true, false>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
+    }
+    if (epi) return launch_tma_f<W, H, THREADS, MINB, false, true>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
+    return launch_tma_f<W, H, THREADS, MINB, false, false>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
+}
+
+template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
+cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute(k_step_tma<S, W, H, THREADS, MINB, DRHO, EPI, FORCE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, TmaCfg<S, W, H, THREADS>::SMEM);
+}
+
+// opt a variant's kernels into their dynamic shared memory (once, outside any
+// stream capture)
+template <int W, int H, int THREADS, int MINB>
+cudaError_t prepare_tma()
 {
     cudaError_t e;
-    if ((e = set_smem_attr<false, false, false>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<false, true, false>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<true, false, false>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<true, true, false>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<false, false, true>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<false, true, true>()) != cudaSuccess) return e;
-    if ((e = set_smem_attr<true, false, true>()) != cudaSuccess) return e;
-    return set_smem_attr<true, true, true>();
+    if ((e = set_attr<W, H, THREADS, MINB, false, false, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<W, H, THREADS, MINB, false, true, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<W, H, THREADS, MINB, true, false, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<W, H, THREADS, MINB, true, true, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<W, H, THREADS, MINB, false, false, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<W, H, THREADS, MINB, false, true, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<W, H, THREADS, MINB, true, false, true>()) != cudaSuccess) return e;
+    return set_attr<W, H, THREADS, MINB, true, true, true>();
 }
 
 template <bool DRHO, bool EPI, bool FORCE>
@@ -60,42 +76,28 @@ cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, con
     return cudaGetLastError();
 }
 
-template <bool DRHO, bool EPI, bool FORCE>
-cudaError_t step_both(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
-                      const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, cudaStream_t s)
-{
-    cudaError_t e = cudaSuccess;
-    if (pl.tma) {
-        if constexpr (TW > 0)
-            e = launch_tma<DRHO, EPI, FORCE>(tsrc, static_cast<S *>(dst), pl, gd, cast_coef<F2>(kd),
-                                             static_cast<float *>(snap), partials, st, s);
-        else
-            e = cudaErrorNotSupported;
-    }
-    if (e == cudaSuccess && pl.n_edge_ctas > 0)
-        e = launch_general<DRHO, EPI, FORCE>(static_cast<const S *>(src), static_cast<S *>(dst), pl, gd,
-                                             cast_coef<T>(kd), static_cast<T *>(snap), partials, st, s);
-    return e;
-}
-
 template <bool DRHO, bool EPI>
-cudaError_t step_f(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
-                   const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool force, cudaStream_t s)
+cudaError_t general_f(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn, double2 *partials,
+                      const DevStatus *st, bool force, cudaStream_t s)
 {
-    if (force) return step_both<DRHO, EPI, true>(src, dst, tsrc, pl, gd, kd, snap, partials, st, s);
-    return step_both<DRHO, EPI, false>(src, dst, tsrc, pl, gd, kd, snap, partials, st, s);
+    if (force) return launch_general<DRHO, EPI, true>(a, b, pl, gd, k, sn, partials, st, s);
+    return launch_general<DRHO, EPI, false>(a, b, pl, gd, k, sn, partials, st, s);
 }
 
-cudaError_t op_step(const void *src, void *dst, const CUtensorMap *tsrc, const Plan &pl, const Grid &gd,
-                    const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
-                    bool force, cudaStream_t s)
+cudaError_t op_step_general(const void *src, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &kd,
+                            void *snap, double2 *partials, const DevStatus *st, bool drho, bool epi, bool force,
+                            cudaStream_t s)
 {
+    const Coef<T> k = cast_coef<T>(kd);
+    const S *a = static_cast<const S *>(src);
+    S *b = static_cast<S *>(dst);
+    T *sn = static_cast<T *>(snap);
     if (drho) {
-        if (epi) return step_f<true, true>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
-        return step_f<true, false>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
+        if (epi) return general_f<true, true>(a, b, pl, gd, k, sn, partials, st, force, s);
+        return general_f<true, false>(a, b, pl, gd, k, sn, partials, st, force, s);
     }
-    if (epi) return step_f<false, true>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
-    return step_f<false, false>(src, dst, tsrc, pl, gd, kd, snap, partials, st, force, s);
+    if (epi) return general_f<false, true>(a, b, pl, gd, k, sn, partials, st, force, s);
+    return general_f<false, false>(a, b, pl, gd, k, sn, partials, st, force, s);
 }
 
 dim3 row_grid(const Grid &gd) { return dim3((gd.nx + 127) / 128, gd.ny, 1); }
@@ -136,8 +138,10 @@ cudaError_t op_mass_partial(const void *src, const Grid &gd, double2 *partials, 
 
 }  // namespace
 
-const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), TW, TH, TW > 0 ? 16 / (int)sizeof(S) : 0,
-                          op_prepare, op_step, op_init_fields, op_fields, op_set_pop, op_get_pop,
-                          op_mass_partial};
+#define PRC_VARIANT(W, H, THREADS, MINB) \
+    { W, H, THREADS, MINB, prepare_tma<W, H, THREADS, MINB>, launch_tma<W, H, THREADS, MINB> }
+
+const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), 16 / (int)sizeof(S), PRC_NVARIANTS, {PRC_VARIANTS},
+                          op_step_general, op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial};
 
 }  // namespace prc

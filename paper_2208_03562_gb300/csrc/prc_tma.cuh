@@ -79,7 +79,7 @@ struct Interior {
     int xlast, ylast;
 };
 
-template <typename S, int W_, int H_>
+template <typename S, int W_, int H_, int THREADS_ = 512>
 struct TmaCfg {
     static constexpr int W = W_, H = H_;
     static constexpr int PADX = 16 / (int)sizeof(S);  // 16-byte aligned box start
@@ -91,7 +91,7 @@ struct TmaCfg {
     static constexpr int RW = W + 4, RH = H + 2;      // density tile: node lx at column lx + 2
     static constexpr int R_BYTES = (RW * RH * 4 + 127) / 128 * 128;
     static constexpr int SMEM = 2 * STAGE_BYTES + R_BYTES + 128 + 128;  // + barriers, + base alignment
-    static constexpr int THREADS = 512;
+    static constexpr int THREADS = THREADS_;
     static constexpr int PAIRS = W / 2;               // node pairs per tile row
 };
 
@@ -133,12 +133,12 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
 
 // Persistent interior kernel: two neighbouring nodes per thread, collision in
 // packed FP32x2 arithmetic.
-template <typename S, int W, int H, bool DRHO, bool EPI, bool FORCE>
-__global__ void __launch_bounds__(512, 1)
+template <typename S, int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
+__global__ void __launch_bounds__(THREADS, MINB)
 k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid gd, Coef<F2> k,
            float *__restrict__ snap, double2 *__restrict__ partials, DevStatus *__restrict__ st, Interior in)
 {
-    using C = TmaCfg<S, W, H>;
+    using C = TmaCfg<S, W, H, THREADS>;
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -258,7 +258,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
         __syncthreads();  // stage `cur` and R are free for reuse
     }
     if constexpr (EPI) {
-        __shared__ double red[2 * 16];
+        __shared__ double red[2 * (THREADS / 32)];
         double a, b;
         acc.block_total(a, b, red);
         if (tid == 0) partials[blockIdx.x] = make_double2(a, b);

@@ -74,6 +74,12 @@ def load():
         "lbm_init_fields": [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
         "lbm_set_populations": [_H, C.c_void_p, C.c_int],
         "lbm_get_populations": [_H, C.c_void_p, C.c_int],
+        "lbm_variant_count": [C.c_int, C.POINTER(C.c_int)],
+        "lbm_variant_info": [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                             C.POINTER(C.c_int)],
+        "lbm_get_variant": [_H, C.POINTER(C.c_int)],
+        "lbm_set_variant": [_H, C.c_int],
+        "lbm_autotune": [_H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
         "lbm_save_bytes": [_H, C.POINTER(C.c_size_t)],
         "lbm_save": [_H, C.c_void_p, C.c_size_t],
         "lbm_load": [_H, C.c_void_p, C.c_size_t],
@@ -98,7 +104,8 @@ def exported_symbols():
                  "lbm_create_p", "lbm_create_ex", "lbm_set_stream", "lbm_destroy", "lbm_last_error",
                  "lbm_step", "lbm_run", "lbm_residual", "lbm_mass", "lbm_info", "lbm_sync", "lbm_fields",
                  "lbm_init_fields", "lbm_set_populations", "lbm_get_populations", "lbm_save_bytes",
-                 "lbm_save", "lbm_load"):
+                 "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
+                 "lbm_set_variant", "lbm_autotune"):
         if hasattr(L, name):
             out.append(name)
     return out
@@ -230,6 +237,39 @@ def lbm_get_populations(h, ny, nx):
     return f
 
 
+def lbm_variant_count(dtype) -> int:
+    n = C.c_int()
+    _check(load().lbm_variant_count(dtype, C.byref(n)))
+    return n.value
+
+
+def lbm_variant_info(dtype, variant):
+    """(tile_w, tile_h, threads, ctas_per_sm) of an interior-kernel variant."""
+    v = [C.c_int() for _ in range(4)]
+    _check(load().lbm_variant_info(dtype, variant, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def lbm_get_variant(h) -> int:
+    v = C.c_int()
+    _check(load().lbm_get_variant(h, C.byref(v)), h)
+    return v.value
+
+
+def lbm_set_variant(h, variant):
+    _check(load().lbm_set_variant(h, int(variant)), h)
+
+
+def lbm_autotune(h, dtype, steps=20):
+    """Time every variant on the handle's grid; selects the fastest.
+    Returns (best, [ms per step of each variant])."""
+    n = lbm_variant_count(dtype)
+    ms = (C.c_double * max(n, 1))()
+    best = C.c_int()
+    _check(load().lbm_autotune(h, int(steps), C.byref(best), ms), h)
+    return best.value, [ms[i] for i in range(n)]
+
+
 def lbm_save(h) -> bytes:
     n = C.c_size_t()
     _check(load().lbm_save_bytes(h, C.byref(n)), h)
@@ -319,6 +359,17 @@ class Lbm:
 
     def populations(self):
         return lbm_get_populations(self.h, self.p.ny, self.p.nx)
+
+    @property
+    def variant(self) -> int:
+        return lbm_get_variant(self.h)
+
+    @variant.setter
+    def variant(self, v):
+        lbm_set_variant(self.h, v)
+
+    def autotune(self, steps=20):
+        return lbm_autotune(self.h, self.p.dtype, steps)
 
     def save(self) -> bytes:
         return lbm_save(self.h)

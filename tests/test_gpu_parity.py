@@ -176,18 +176,36 @@ def test_interior_kernel_matches_oracle(case, dtype):
     assert rel_l2_u(a, b) < (1e-5 if dtype == L.F32 else 1e-3)
 
 
-def test_interior_and_general_paths_agree(monkeypatch):
-    """The TMA interior kernel and the general kernel run the same collision;
-    on the same input they agree to FP32 round-off."""
+@pytest.mark.parametrize("dtype", [L.F32, L.F16])
+def test_every_variant_agrees_with_general_kernel(dtype):
+    """Every compiled shape of the interior kernel and the general kernel run
+    the same collision; on the same input they agree to round-off."""
     out = []
-    for env in ("0", "1"):
-        monkeypatch.setenv("PRC_LBM_GENERAL_ONLY", env)
-        g, o = pair(330, 140, 0.5, 0.3, 0.01, 0.04, L.F32)
+    for v in range(-1, L.lbm_variant_count(dtype)):
+        g, o = pair(330, 140, 0.5, 0.3, 0.01, 0.04, dtype)
+        g.variant = v
+        assert g.variant == v
         random_start(g, o, seed=9, amp=1e-3)
         g.step(45)
-        out.append((g.populations(), g.residual()))
-    assert np.max(np.abs(out[0][0] - out[1][0])) < 1e-7
-    assert abs(out[0][1] - out[1][1]) <= 1e-5 * out[1][1]
+        out.append((v, g.populations(), g.residual()))
+    tol = 1e-7 if dtype == L.F32 else 2e-5
+    for v, f, r in out[1:]:
+        assert np.max(np.abs(f - out[0][1])) < tol, v
+        assert abs(r - out[0][2]) <= 1e-4 * out[0][2], v
+
+
+def test_autotune_restores_state_exactly():
+    g, _ = pair(520, 260, 0.5, 0.3, 0.01, 0.04, L.F32)
+    g.step(33)
+    before = g.populations()
+    info = g.info()
+    best, ms = g.autotune(10)
+    assert 0 <= best < len(ms) and all(m > 0 for m in ms)
+    assert g.variant == best
+    assert np.array_equal(before, g.populations())
+    assert g.info().step == info.step and g.info().residual == info.residual
+    g.step(7)
+    assert np.all(np.isfinite(g.populations()))
 
 
 def test_fp32_residual_matches_oracle():
