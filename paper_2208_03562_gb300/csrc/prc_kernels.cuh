@@ -39,6 +39,10 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
     const int x0 = rc.x0[r] + (lt % rc.tiles_x[r]) * BX, y0 = rc.y0[r] + (lt / rc.tiles_x[r]) * BY;
     const int x = x0 + tx, y = y0 + ty;
     const bool valid = (x < rc.x1[r]) & (y < rc.y1[r]);
+    T snap_old = T(0);
+    if constexpr (EPI) {  // issue early: overlaps the pulls
+        if (valid) snap_old = __ldcs(snap + (long long)y * gd.pitch + x);
+    }
 
     T g[9];
     int mx = x, my = y;
@@ -84,8 +88,8 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
         RedAcc<T> acc;
         if (valid) {
             const long long o = (long long)y * gd.pitch + x;
-            const T d = ux - snap[o];
-            snap[o] = ux;
+            const T d = ux - snap_old;
+            __stcs(snap + o, ux);
             acc.add(d * d, drho);
         }
         double a, b;

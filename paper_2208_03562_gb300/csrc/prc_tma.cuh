@@ -172,6 +172,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
     };
 
     RedAcc<float> acc;
+    constexpr int NQ = (H * C::PAIRS + C::THREADS - 1) / C::THREADS;  // node pairs per thread per tile
+    float2 snv[EPI ? NQ : 1];  // residual snapshot of this thread's pairs, prefetched
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) issue(tile, stage0, &bar[0]);
     bool in_flight_other = false;  // (thread 0) a copy into the other stage is outstanding
@@ -184,6 +186,19 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
             in_flight_other = next < ntiles;
             if (in_flight_other) issue(next, s ? stage0 : stage1, &bar[s ^ 1]);
         }
+        int x0, y0, ox, oy;
+        origin(tile, x0, y0, ox, oy);
+        if constexpr (EPI) {
+            // the snapshot is touched once per residual step: stream it, and
+            // issue the loads now so that they overlap the copies and the collision
+#pragma unroll
+            for (int j = 0; j < NQ; j++) {
+                const int q = tid + j * C::THREADS;
+                const int ly = q / C::PAIRS, x = 2 * (q - ly * C::PAIRS);
+                if (q < H * C::PAIRS && x0 + x >= ox && y0 + ly >= oy)
+                    snv[j] = __ldcs(reinterpret_cast<const float2 *>(snap + (long long)(y0 + ly) * gd.pitch + x0 + x));
+            }
+        }
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -194,8 +209,6 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
             __syncthreads();
             return;
         }
-        int x0, y0, ox, oy;
-        origin(tile, x0, y0, ox, oy);
 
         if constexpr (DRHO) {
             // density (minus rho0) of the tile rows and the ring rows, by pairs
@@ -217,7 +230,10 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
             __syncthreads();
         }
 
-        for (int q = tid; q < H * C::PAIRS; q += C::THREADS) {
+#pragma unroll
+        for (int j = 0; j < NQ; j++) {
+            const int q = tid + j * C::THREADS;
+            if (q >= H * C::PAIRS) break;
             const int ly = q / C::PAIRS, x = 2 * (q - ly * C::PAIRS);
             F2 g[9];
             pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
@@ -247,9 +263,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
             for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[i]);
             if constexpr (EPI) {
                 if (x0 + x >= ox && y0 + ly >= oy) {  // the pair is owned by this tile
-                    const float2 sn = *reinterpret_cast<const float2 *>(snap + o);
-                    *reinterpret_cast<float2 *>(snap + o) = ux.v;
-                    const float da = ux.v.x - sn.x, db = ux.v.y - sn.y;
+                    __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
+                    const float da = ux.v.x - snv[j].x, db = ux.v.y - snv[j].y;
                     acc.add(da * da, drho.v.x);
                     acc.add(db * db, drho.v.y);
                 }
