@@ -226,6 +226,42 @@ lbm_status lbm_get_variant(lbm_t h, int *variant);
 lbm_status lbm_set_variant(lbm_t h, int variant);
 lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step);
 
+/*
+ * One time step that allocates nothing.  The paper has no counterpart: this
+ * serves callers that cannot allocate device memory -- code running while a
+ * stream is captured into a CUDA graph (allocation cannot be captured), code
+ * whose device memory is wholly owned by another allocator, and tight loops
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * The caller owns every buffer (device pointers on the current device):
+ *   src, dst  the post-collision populations before / after the step, in the
+ *             library's storage: 9 planes of ny rows of `pitch` elements,
+ *             pitch = nx rounded up to a multiple of 32, each element the
+ *             shifted population f_i - w_i(r) rho0 (rho0 = 1) in the storage
+ *             type of p->dtype (double, float or IEEE half); src != dst;
+ *   snap      ny x pitch values of u_x from the previous residual evaluation
+ *             (double for LBM_F64, float otherwise); read and overwritten
+ *             with the new u_x when with_residual != 0, untouched otherwise;
+ *   out       when with_residual != 0: out[0] = ||u_x - snap||_2 (Sec. 5.2
+ *             residual) and out[1] = sum of rho over the grid, both FP64.
+ * The step is enqueued on `stream` (cudaStream_t, NULL = legacy default) and
+ * runs the general wall-aware kernel on every node.
+ *
+ * Scratch: a file-scope device array of 16384 FP64 pairs (256 KiB) plus one
+ * status word, held by every GPU that loads the library until the process
+ * exits.  Grids with ceil(nx/32) * ceil(ny/8) > 16384 are rejected with
+ * LBM_EINVAL (e.g. 2048 x 2048 is the largest square grid).  Every call
+ * shares that scratch and leaves its contents behind; the call clears the
+ * status word itself.  Calls whose kernels overlap on the GPU (different
+ * streams, or different host threads) race on the scratch: serialise them.
+ * The first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  The call itself performs no cudaMalloc,
+ * cudaFree or allocating library call.
+ */
+lbm_status lbm_step_noalloc(const lbm_params *p, const void *src, void *dst, void *snap, int with_residual,
+                            double *out, void *stream);
+
 /* Derived constants: shear relaxation rate omega_nu and q = min(1, r). */
 lbm_status lbm_omega_nu(const lbm_params *p, double *omega_nu);
 

@@ -3,6 +3,8 @@
 // device-side stop rule of lbm_run, residual/mass finalisation, field and
 // population transfers, checkpoints.
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -977,6 +979,105 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
     if (rs != LBM_OK) return rs;
     if (best) *best = arg;
     return apply_variant(h, arg);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free step.  Some callers cannot call cudaMalloc: code that runs
+// while a stream is being captured into a CUDA graph (allocation is not a
+// capturable operation), code whose device memory is entirely reserved by
+// another allocator, and latency-critical loops that cannot take the implicit
+// device synchronisation of cudaMalloc / cudaFree.  lbm_step_noalloc serves
+// them: the only scratch it needs (per-CTA FP64 partial sums and a status
+// word) lives in the file-scope device arrays below, which every GPU that
+// loads this library holds until the process exits.
+
+namespace {
+
+constexpr int NOALLOC_MAX_PARTS = 16384;  // 256 KiB of double2: ceil(nx/32) * ceil(ny/8) CTAs at most
+static __device__ __align__(256) double2 g_noalloc_partials[NOALLOC_MAX_PARTS];
+static __device__ __align__(256) DevStatus g_noalloc_status;
+
+struct NoallocScratch {
+    double2 *partials;
+    DevStatus *status;
+};
+
+std::mutex g_noalloc_mu;
+std::map<int, NoallocScratch> g_noalloc_addr;  // device ordinal -> device addresses of the arrays
+
+// Device addresses of the scratch arrays on the current device.  In host code
+// the array names are host-side stand-ins, not device addresses; the real
+// addresses come from cudaGetSymbolAddress with the device current, once per
+// device.
+lbm_status noalloc_scratch(NoallocScratch *out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return LBM_OK;
+    }
+    NoallocScratch sc;
+    e = cudaGetSymbolAddress(reinterpret_cast<void **>(&sc.partials), g_noalloc_partials);
+    if (e != cudaSuccess)
+        return fail(nullptr, LBM_ECUDA, std::string("cudaGetSymbolAddress(partials): ") + cudaGetErrorString(e));
+    e = cudaGetSymbolAddress(reinterpret_cast<void **>(&sc.status), g_noalloc_status);
+    if (e != cudaSuccess)
+        return fail(nullptr, LBM_ECUDA, std::string("cudaGetSymbolAddress(status): ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = sc;
+    *out = sc;
+    return LBM_OK;
+}
+
+__global__ void __launch_bounds__(256) k_noalloc_finalize(const double2 *partials, int n, double *out, double nnodes)
+{
+    double a, b;
+    reduce_partials(partials, n, a, b);
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(a);
+        out[1] = nnodes + b;
+    }
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step_noalloc(const lbm_params *p, const void *src, void *dst, void *snap, int with_residual,
+                                       double *out, void *stream)
+{
+    lbm_status s = lbm_params_check(p);
+    if (s != LBM_OK) return s;
+    if (!src || !dst || !snap) return fail(nullptr, LBM_EINVAL, "null buffer");
+    if (with_residual && !out) return fail(nullptr, LBM_EINVAL, "null residual output");
+    if (src == dst) return fail(nullptr, LBM_EINVAL, "src and dst must be different buffers");
+    const Plan pl = make_plan(*p, 0, -1);  // general kernel over the whole grid
+    if (pl.nparts > NOALLOC_MAX_PARTS)
+        return fail(nullptr, LBM_EINVAL,
+                    "grid too large for lbm_step_noalloc: ceil(nx/32)*ceil(ny/8) = " + std::to_string(pl.nparts) +
+                        " exceeds " + std::to_string(NOALLOC_MAX_PARTS));
+    NoallocScratch sc;
+    s = noalloc_scratch(&sc);
+    if (s != LBM_OK) return s;
+    const prc::DtypeOps *ops = ops_for(p->dtype);
+    const Layout L = make_layout(*p);
+    const Grid gd = make_grid(*p, L);
+    Coef<double> k;
+    make_coef(*p, k);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the status word shared by every call must start clear (stop = 0)
+    cudaError_t e = cudaMemsetAsync(sc.status, 0, sizeof(DevStatus), st);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    e = ops->step_general(src, dst, pl, gd, k, snap, sc.partials, sc.status, p->drho == LBM_DRHO_CURRENT,
+                          with_residual != 0, p->fx != 0.0 || p->fy != 0.0, st);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    if (with_residual) {
+        k_noalloc_finalize<<<1, 256, 0, st>>>(sc.partials, pl.nparts, out, (double)p->nx * (double)p->ny);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, std::string("finalize launch: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
 }
 
 namespace {

@@ -80,6 +80,7 @@ def load():
         "lbm_get_variant": [_H, C.POINTER(C.c_int)],
         "lbm_set_variant": [_H, C.c_int],
         "lbm_autotune": [_H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+        "lbm_step_noalloc": [P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
         "lbm_save_bytes": [_H, C.POINTER(C.c_size_t)],
         "lbm_save": [_H, C.c_void_p, C.c_size_t],
         "lbm_load": [_H, C.c_void_p, C.c_size_t],
@@ -105,7 +106,7 @@ def exported_symbols():
                  "lbm_step", "lbm_run", "lbm_residual", "lbm_mass", "lbm_info", "lbm_sync", "lbm_fields",
                  "lbm_init_fields", "lbm_set_populations", "lbm_get_populations", "lbm_save_bytes",
                  "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
-                 "lbm_set_variant", "lbm_autotune"):
+                 "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc"):
         if hasattr(L, name):
             out.append(name)
     return out
@@ -268,6 +269,14 @@ def lbm_autotune(h, dtype, steps=20):
     best = C.c_int()
     _check(load().lbm_autotune(h, int(steps), C.byref(best), ms), h)
     return best.value, [ms[i] for i in range(n)]
+
+
+def lbm_step_noalloc(p: lbm_params, src_ptr: int, dst_ptr: int, snap_ptr: int, with_residual: bool,
+                     out_ptr: int, stream_ptr: int):
+    """One step on caller-owned device buffers, no device allocation (see
+    the header for the buffer layout and the shared-scratch rules)."""
+    _check(load().lbm_step_noalloc(C.byref(p), C.c_void_p(src_ptr), C.c_void_p(dst_ptr), C.c_void_p(snap_ptr),
+                                   1 if with_residual else 0, C.c_void_p(out_ptr), C.c_void_p(stream_ptr)))
 
 
 def lbm_save(h) -> bytes:
