@@ -262,6 +262,58 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step);
 lbm_status lbm_step_noalloc(const lbm_params *p, const void *src, void *dst, void *snap, int with_residual,
                             double *out, void *stream);
 
+/*
+ * Batched engine.  A batch holds up to `capacity` independent instances
+ * (slots) of one storage type, each with its own grid, parameters, residual
+ * tolerance and step limit (for example the uneven cavities of a parameter
+ * sweep, or the requests of a solve server).  lbm_batch_launch advances every
+ * active slot with ONE persistent cooperative kernel launch (through a
+ * captured CUDA graph when use_graph != 0): each step sweeps the 32 x 8 node
+ * tiles of all active slots with the wall-aware fused update, a bounded grid
+ * barrier separates the steps, and every slot evaluates its FP64 residual on
+ * its own step counter (every 20 steps, Sec. 5.2).  A slot retires on the
+ * device as soon as its residual is below its tolerance (CONVERGED), is not
+ * finite (DIVERGED) or it reached its step limit (MAXSTEPS); the others
+ * continue.  An instance's results do not depend on the other slots: its
+ * sums are reduced in a fixed order over its own tiles.  Slots may be added
+ * and removed between launches (continuous batching); adding allocates the
+ * slot's memory stream-ordered (lbm_batch_instance_bytes tells how much) and
+ * returns ENOMEM when the device is full.  A launch is asynchronous; call
+ * lbm_batch_wait before touching slots again.  A barrier that runs out
+ * (about two seconds) ends the launch with LBM_ETIMEOUT.
+ */
+typedef struct lbm_batch_s *lbm_batch_t;
+
+typedef enum {
+    LBM_SLOT_ACTIVE = 0,
+    LBM_SLOT_CONVERGED = 1,
+    LBM_SLOT_DIVERGED = 2,
+    LBM_SLOT_MAXSTEPS = 3,
+    LBM_SLOT_EMPTY = 4
+} lbm_slot_state;
+
+lbm_status lbm_batch_create(int capacity, int dtype, void *stream, lbm_batch_t *out);
+void lbm_batch_destroy(lbm_batch_t b);
+const char *lbm_batch_last_error(lbm_batch_t b);
+lbm_status lbm_batch_instance_bytes(const lbm_params *p, size_t *bytes);
+/* Fill a free slot with an instance at rest; *slot receives its index. */
+lbm_status lbm_batch_add(lbm_batch_t b, const lbm_params *p, double tol, long max_steps, int *slot);
+lbm_status lbm_batch_remove(lbm_batch_t b, int slot);
+/* Advance every active slot by up to `steps` steps (one persistent launch). */
+lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph);
+/* Wait for the launch; *n_active receives the slots still active. */
+lbm_status lbm_batch_wait(lbm_batch_t b, int *n_active);
+/* lbm_batch_launch(use_graph = 1) + lbm_batch_wait. */
+lbm_status lbm_batch_run(lbm_batch_t b, long steps, int *n_active);
+/* Progress of a slot (as of the last wait) and its lbm_slot_state. */
+lbm_status lbm_batch_query(lbm_batch_t b, int slot, lbm_info_t *info, int *state);
+/* Fields / populations of a slot, conventions as lbm_fields and
+ * lbm_set_populations (setting resets the slot's step counter and makes it
+ * active). */
+lbm_status lbm_batch_fields(lbm_batch_t b, int slot, double *rho, double *ux, double *uy, int on_device);
+lbm_status lbm_batch_set_populations(lbm_batch_t b, int slot, const double *f, int on_device);
+lbm_status lbm_batch_get_populations(lbm_batch_t b, int slot, double *f, int on_device);
+
 /* Derived constants: shear relaxation rate omega_nu and q = min(1, r). */
 lbm_status lbm_omega_nu(const lbm_params *p, double *omega_nu);
 

@@ -1,0 +1,199 @@
+// prc_batch.cuh -- many independent cavities in one persistent launch.
+//
+// A batch is a table of instances, each with its own grid, parameters,
+// population sets, residual snapshot and step counter.  One cooperative launch
+// of k_batch advances every active instance by up to `steps` time steps: in
+// each step the CTAs sweep the BX x BY tiles of all active instances (general
+// wall-aware tile body), a grid barrier separates the steps, and after each
+// residual step (every 20 steps of an instance's own counter) one CTA per
+// instance reduces that instance's per-tile partial sums in a fixed order,
+// so an instance's result does not depend on the other instances of the mix.
+// An instance retires when its residual falls below its tolerance, when it
+// diverges, or when it reaches its step limit; its tiles are skipped from the
+// next step on.  The grid barrier is a bounded spin: when it runs out it
+// records LBM_ETIMEOUT and every CTA leaves.
+#pragma once
+
+#include "prc_kernels.cuh"
+
+namespace prc {
+
+enum BatchState : int { BATCH_ACTIVE = 0, BATCH_CONVERGED = 1, BATCH_DIVERGED = 2, BATCH_MAXSTEPS = 3, BATCH_EMPTY = 4 };
+
+// Read-only part of an instance descriptor (set by the host before a launch).
+struct BatchInst {
+    int slot;           // index into the per-slot tables (coefficients, dynamic state)
+    int pad;
+    void *pop[2];       // population sets A / B (state in pop[t & 1])
+    void *snap;         // residual snapshot (u_x), collision precision
+    Grid gd;
+    int tiles_x, tiles;  // BX x BY tiling of the grid
+    int tile_start;      // first global tile index of this instance in the launch
+    int part_base;       // first partial-sum slot
+    int drho, force;
+    double tol;
+    long long max_steps;
+};
+
+// Mutable part, updated on the device.
+struct BatchDyn {
+    long long t;         // completed steps
+    long long res_step;  // step of the last residual
+    double res, mass;
+    int state;
+    int pad;
+};
+
+struct BatchCtl {
+    unsigned arrive;     // grid barrier
+    unsigned gen;
+    int error;           // 1: barrier timeout
+    int pad;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier for a cooperative (co-resident) launch; false when it
+// timed out or another CTA reported an error.
+__device__ __forceinline__ bool grid_barrier(BatchCtl *ctl)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        ok = 1;
+        const unsigned g = ld_acquire_u32(&ctl->gen);
+        __threadfence();
+        const unsigned n = gridDim.x;
+        if (atomicAdd(&ctl->arrive, 1u) == n - 1) {
+            atomicExch(&ctl->arrive, 0u);
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&ctl->gen) == g) {
+                if (ld_relaxed_i32(&ctl->error)) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > 4000000000LL) {  // about two seconds
+                    atomicExch(&ctl->error, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
+__device__ __forceinline__ void batch_tile_t(const BatchInst &I, const Coef<T> &k, int parity, int lt,
+                                             double2 *partials)
+{
+    const int x0 = (lt % I.tiles_x) * BX, y0 = (lt / I.tiles_x) * BY;
+    general_tile<S, T, DRHO, EPI, FORCE, true>(static_cast<const S *>(I.pop[parity]), static_cast<S *>(I.pop[parity ^ 1]),
+                                         I.gd, k, static_cast<T *>(I.snap), x0, y0, I.gd.nx, I.gd.ny,
+                                         partials + I.part_base + lt);
+}
+
+template <typename S, typename T>
+__device__ __forceinline__ void batch_tile(const BatchInst &I, const Coef<T> &k, int parity, int lt, bool epi,
+                                           double2 *partials)
+{
+    if (I.drho) {
+        if (I.force) {
+            if (epi) batch_tile_t<S, T, true, true, true>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, true, false, true>(I, k, parity, lt, partials);
+        } else {
+            if (epi) batch_tile_t<S, T, true, true, false>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, true, false, false>(I, k, parity, lt, partials);
+        }
+    } else {
+        if (I.force) {
+            if (epi) batch_tile_t<S, T, false, true, true>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, false, false, true>(I, k, parity, lt, partials);
+        } else {
+            if (epi) batch_tile_t<S, T, false, true, false>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, false, false, false>(I, k, parity, lt, partials);
+        }
+    }
+}
+
+template <typename S, typename T>
+__global__ void __launch_bounds__(BX * BY)
+k_batch(const BatchInst *__restrict__ inst, const Coef<T> *__restrict__ coefs, BatchDyn *dyn, int ninst,
+        int total_tiles, double2 *partials, BatchCtl *ctl, int steps)
+{
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int s = 0; s < steps; s++) {
+        // ---- one time step of every active instance
+        int i = 0;
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+            while (i + 1 < ninst && tile >= inst[i + 1].tile_start) i++;  // tiles are in instance order
+            const BatchInst &I = inst[i];
+            BatchDyn *D = dyn + I.slot;
+            if (ld_relaxed_i32(&D->state) != BATCH_ACTIVE) continue;
+            const long long t = __ldcg(&D->t);
+            const bool epi = ((t + 1) % 20) == 0;
+            batch_tile<S, T>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start, epi, partials);
+        }
+        if (!grid_barrier(ctl)) return;
+        // ---- bookkeeping: counters, residuals, retirement (one CTA per instance)
+        for (int j = blockIdx.x; j < ninst; j += gridDim.x) {
+            const BatchInst &I = inst[j];
+            BatchDyn *D = dyn + I.slot;
+            if (ld_relaxed_i32(&D->state) != BATCH_ACTIVE) continue;
+            const long long t = __ldcg(&D->t) + 1;
+            if (t % 20 == 0) {
+                __shared__ double sa[BX * BY], sb[BX * BY];
+                double a = 0.0, b = 0.0;
+                for (int q = tid; q < I.tiles; q += BX * BY) {
+                    const double2 v = __ldcg(partials + I.part_base + q);
+                    a += v.x;
+                    b += v.y;
+                }
+                sa[tid] = a;
+                sb[tid] = b;
+                __syncthreads();
+                for (int w = (BX * BY) / 2; w > 0; w >>= 1) {
+                    if (tid < w) {
+                        sa[tid] += sa[tid + w];
+                        sb[tid] += sb[tid + w];
+                    }
+                    __syncthreads();
+                }
+                if (tid == 0) {
+                    const double res = sqrt(sa[0]), mass = (double)I.gd.nx * (double)I.gd.ny + sb[0];
+                    D->res = res;
+                    D->mass = mass;
+                    D->res_step = t;
+                    if (!isfinite(res) || !isfinite(mass)) D->state = BATCH_DIVERGED;
+                    else if (res < I.tol) D->state = BATCH_CONVERGED;
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                D->t = t;
+                if (D->state == BATCH_ACTIVE && t >= I.max_steps) D->state = BATCH_MAXSTEPS;
+            }
+        }
+        if (!grid_barrier(ctl)) return;
+    }
+}
+
+}  // namespace prc

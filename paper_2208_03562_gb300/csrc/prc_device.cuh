@@ -87,6 +87,20 @@ template <> __device__ __forceinline__ double ld_s<double, double>(const double 
 template <> __device__ __forceinline__ float ld_s<float, float>(const float *p) { return __ldg(p); }
 template <> __device__ __forceinline__ float ld_s<__half, float>(const __half *p) { return __half2float(__ldg(p)); }
 
+// L2-coherent loads (ld.global.cg) for data written by other CTAs of the same
+// persistent launch
+template <typename S, typename T> __device__ __forceinline__ T ld_cg(const S *p);
+template <> __device__ __forceinline__ double ld_cg<double, double>(const double *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<float, float>(const float *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float ld_cg<__half, float>(const __half *p) { return __half2float(__ldcg(p)); }
+
+template <bool CG, typename S, typename T>
+__device__ __forceinline__ T ld_pop(const S *p)
+{
+    if constexpr (CG) return ld_cg<S, T>(p);
+    else return ld_s<S, T>(p);
+}
+
 template <typename S, typename T> __device__ __forceinline__ S to_s(T v);
 template <> __device__ __forceinline__ double to_s<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ float to_s<float, float>(float v) { return v; }
@@ -107,7 +121,7 @@ __device__ __forceinline__ void map_node(const Grid &gd, int &x, int &y)
 // bounce-back: a source outside a wall is replaced by the opposite population
 // of the node itself, plus the moving-top-wall term -/+ c^2 U / (2 r^2) on the
 // two diagonal links that come from above (directions SW, SE).
-template <typename S, typename T>
+template <typename S, typename T, bool CG = false>
 __device__ __forceinline__ void pull9(const S *__restrict__ src, const Grid &gd, int x, int y, T lid, T g[9])
 {
 #pragma unroll
@@ -117,9 +131,9 @@ __device__ __forceinline__ void pull9(const S *__restrict__ src, const Grid &gd,
         if (gd.bc == 2) sy = sy < 0 ? sy + gd.ny : (sy >= gd.ny ? sy - gd.ny : sy);
         bool inside = (sx >= 0) & (sx < gd.nx) & (sy >= 0) & (sy < gd.ny);
         if (inside) {
-            g[i] = ld_s<S, T>(src + (long long)i * gd.plane + (long long)sy * gd.pitch + sx);
+            g[i] = ld_pop<CG, S, T>(src + (long long)i * gd.plane + (long long)sy * gd.pitch + sx);
         } else {
-            T v = ld_s<S, T>(src + (long long)opp_of(i) * gd.plane + (long long)y * gd.pitch + x);
+            T v = ld_pop<CG, S, T>(src + (long long)opp_of(i) * gd.plane + (long long)y * gd.pitch + x);
             if (sy >= gd.ny && gd.lid_on) {
                 if (i == 7) v -= lid;
                 if (i == 8) v += lid;

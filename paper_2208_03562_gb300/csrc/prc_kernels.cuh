@@ -21,24 +21,20 @@ struct Rects {
     int start[5];  // first tile index of each rectangle; start[n] = total
 };
 
-// One fused time step on the nodes of `rc`: pull-stream + walls, density tile
-// (+1 ring) in shared memory for the density gradient, collision, store.  With
-// EPI the step also accumulates (u_x - u_x,snapshot)^2 and drho per CTA for the
-// residual of Sec. 5.2 and refreshes the snapshot; the CTA totals go to
-// partials[part0 + blockIdx.x].
-template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
-__global__ void __launch_bounds__(BX * BY)
-k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
-       double2 *__restrict__ partials, const DevStatus *__restrict__ st, Rects rc, int part0)
+// One fused time step on one BX x BY tile at (x0, y0) of the nodes x < x1,
+// y < y1: pull-stream + walls, density tile (+1 ring) in shared memory for the
+// density gradient, collision, store.  With EPI the tile also accumulates
+// (u_x - u_x,snapshot)^2 and drho for the residual of Sec. 5.2, refreshes the
+// snapshot and writes its FP64 totals to *part_out.  Called by all BX x BY
+// threads of a CTA.
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool CG = false>
+__device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__restrict__ dst, const Grid &gd,
+                                             const Coef<T> &k, T *__restrict__ snap, int x0, int y0, int x1, int y1,
+                                             double2 *part_out)
 {
-    if (st->stop) return;
-    int r = 0;
-    while (r + 1 < rc.n && (int)blockIdx.x >= rc.start[r + 1]) r++;
-    const int lt = blockIdx.x - rc.start[r];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = rc.x0[r] + (lt % rc.tiles_x[r]) * BX, y0 = rc.y0[r] + (lt / rc.tiles_x[r]) * BY;
     const int x = x0 + tx, y = y0 + ty;
-    const bool valid = (x < rc.x1[r]) & (y < rc.y1[r]);
+    const bool valid = (x < x1) & (y < y1);
     T snap_old = T(0);
     if constexpr (EPI) {  // issue early: overlaps the pulls
         if (valid) snap_old = __ldcs(snap + (long long)y * gd.pitch + x);
@@ -47,7 +43,7 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
     T g[9];
     int mx = x, my = y;
     map_node(gd, mx, my);
-    pull9<S, T>(src, gd, mx, my, k.lid, g);
+    pull9<S, T, CG>(src, gd, mx, my, k.lid, g);
 
     T dxr = T(0), dyr = T(0);
     if constexpr (DRHO) {
@@ -63,7 +59,7 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
             int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
             map_node(gd, gx, gy);
             T gr[9];
-            pull9<S, T>(src, gd, gx, gy, k.lid, gr);
+            pull9<S, T, CG>(src, gd, gx, gy, k.lid, gr);
             srho[ly][lx] = sum9(gr);
         }
         __syncthreads();
@@ -74,6 +70,7 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
         const T rSE = srho[cy - 1][cx + 1], rSW = srho[cy - 1][cx - 1];
         dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
         dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+        __syncthreads();  // srho may be refilled by the next tile of this CTA
     }
 
     T ux = T(0), uy = T(0), drho = T(0);
@@ -94,8 +91,25 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
         }
         double a, b;
         acc.block_total(a, b, red);
-        if (ty == 0 && tx == 0) partials[part0 + blockIdx.x] = make_double2(a, b);
+        if (ty == 0 && tx == 0) *part_out = make_double2(a, b);
+        __syncthreads();  // red may be reused by the next tile of this CTA
     }
+}
+
+// One fused time step on the nodes of `rc` (general kernel); the CTA totals
+// of a residual step go to partials[part0 + blockIdx.x].
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
+__global__ void __launch_bounds__(BX * BY)
+k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
+       double2 *__restrict__ partials, const DevStatus *__restrict__ st, Rects rc, int part0)
+{
+    if (st->stop) return;
+    int r = 0;
+    while (r + 1 < rc.n && (int)blockIdx.x >= rc.start[r + 1]) r++;
+    const int lt = blockIdx.x - rc.start[r];
+    const int x0 = rc.x0[r] + (lt % rc.tiles_x[r]) * BX, y0 = rc.y0[r] + (lt / rc.tiles_x[r]) * BY;
+    general_tile<S, T, DRHO, EPI, FORCE>(src, dst, gd, k, snap, x0, y0, rc.x1[r], rc.y1[r],
+                                         partials + part0 + blockIdx.x);
 }
 
 // f~ = f^eq(rho, u) (Eq. 12, uncorrected), stored shifted; snapshot = u_x.

@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "prc_batch.cuh"
 #include "prc_kernels.cuh"
 #include "prc_tma.cuh"
 
@@ -56,6 +57,12 @@ struct DtypeOps {
     cudaError_t (*step_general)(const void *src, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &k,
                                 void *snap, double2 *partials, const DevStatus *st, bool drho, bool epi, bool force,
                                 cudaStream_t s);
+    // batch: per-slot coefficient conversion, occupancy and the persistent launch
+    size_t coef_bytes;
+    void (*coef_convert)(const Coef<double> &in, void *out);
+    cudaError_t (*batch_occupancy)(int *blocks_per_sm);
+    cudaError_t (*batch_launch)(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int total_tiles,
+                                double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s);
     cudaError_t (*init_fields)(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
                                const double *ux, const double *uy, void *snap, cudaStream_t s);
     cudaError_t (*fields)(const void *src, const Grid &gd, const Coef<double> &k, double *rho, double *ux,

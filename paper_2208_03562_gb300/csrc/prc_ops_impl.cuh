@@ -100,6 +100,23 @@ cudaError_t op_step_general(const void *src, void *dst, const Plan &pl, const Gr
     return general_f<false, false>(a, b, pl, gd, k, sn, partials, st, force, s);
 }
 
+void op_coef_convert(const Coef<double> &in, void *out) { *static_cast<Coef<T> *>(out) = cast_coef<T>(in); }
+
+cudaError_t op_batch_occupancy(int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<S, T>, BX * BY, 0);
+}
+
+// one cooperative launch (all CTAs co-resident, as the grid barrier needs)
+cudaError_t op_batch_launch(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int total_tiles,
+                            double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s)
+{
+    const Coef<T> *cf = static_cast<const Coef<T> *>(coefs);
+    void *args[] = {(void *)&inst, (void *)&cf, (void *)&dyn, (void *)&ninst, (void *)&total_tiles,
+                    (void *)&partials, (void *)&ctl, (void *)&steps};
+    return cudaLaunchCooperativeKernel((const void *)k_batch<S, T>, dim3(grid), dim3(BX, BY), args, 0, s);
+}
+
 dim3 row_grid(const Grid &gd) { return dim3((gd.nx + 127) / 128, gd.ny, 1); }
 
 cudaError_t op_init_fields(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
@@ -142,6 +159,7 @@ cudaError_t op_mass_partial(const void *src, const Grid &gd, double2 *partials, 
     { W, H, THREADS, MINB, prepare_tma<W, H, THREADS, MINB>, launch_tma<W, H, THREADS, MINB> }
 
 const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), 16 / (int)sizeof(S), PRC_NVARIANTS, {PRC_VARIANTS},
-                          op_step_general, op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial};
+                          op_step_general, sizeof(Coef<T>), op_coef_convert, op_batch_occupancy, op_batch_launch,
+                          op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial};
 
 }  // namespace prc

@@ -85,6 +85,20 @@ def load():
         "lbm_save": [_H, C.c_void_p, C.c_size_t],
         "lbm_load": [_H, C.c_void_p, C.c_size_t],
     }
+    B = C.c_void_p
+    sig.update({
+        "lbm_batch_create": [C.c_int, C.c_int, C.c_void_p, C.POINTER(B)],
+        "lbm_batch_instance_bytes": [P, C.POINTER(C.c_size_t)],
+        "lbm_batch_add": [B, P, C.c_double, C.c_long, C.POINTER(C.c_int)],
+        "lbm_batch_remove": [B, C.c_int],
+        "lbm_batch_launch": [B, C.c_long, C.c_int],
+        "lbm_batch_wait": [B, C.POINTER(C.c_int)],
+        "lbm_batch_run": [B, C.c_long, C.POINTER(C.c_int)],
+        "lbm_batch_query": [B, C.c_int, C.POINTER(lbm_info_t), C.POINTER(C.c_int)],
+        "lbm_batch_fields": [B, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
+        "lbm_batch_set_populations": [B, C.c_int, C.c_void_p, C.c_int],
+        "lbm_batch_get_populations": [B, C.c_int, C.c_void_p, C.c_int],
+    })
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
@@ -93,6 +107,10 @@ def load():
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [_H]
     L.lbm_last_error.restype = C.c_char_p
+    L.lbm_batch_destroy.argtypes = [C.c_void_p]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_last_error.argtypes = [C.c_void_p]
+    L.lbm_batch_last_error.restype = C.c_char_p
     _lib = L
     return L
 
@@ -106,7 +124,10 @@ def exported_symbols():
                  "lbm_step", "lbm_run", "lbm_residual", "lbm_mass", "lbm_info", "lbm_sync", "lbm_fields",
                  "lbm_init_fields", "lbm_set_populations", "lbm_get_populations", "lbm_save_bytes",
                  "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
-                 "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc"):
+                 "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc", "lbm_batch_create",
+                 "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_instance_bytes", "lbm_batch_add",
+                 "lbm_batch_remove", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
+                 "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations"):
         if hasattr(L, name):
             out.append(name)
     return out
@@ -385,3 +406,88 @@ class Lbm:
 
     def load(self, blob: bytes):
         lbm_load(self.h, blob)
+
+
+# ---------------------------------------------------------------------------
+# batched engine
+
+SLOT_ACTIVE, SLOT_CONVERGED, SLOT_DIVERGED, SLOT_MAXSTEPS, SLOT_EMPTY = range(5)
+SLOT_NAMES = ["ACTIVE", "CONVERGED", "DIVERGED", "MAXSTEPS", "EMPTY"]
+
+
+def _bcheck(status, b):
+    if status != OK:
+        msg = load().lbm_batch_last_error(b)
+        raise LbmError(status, msg.decode() if msg else "")
+    return status
+
+
+def lbm_batch_instance_bytes(p: lbm_params) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_batch_instance_bytes(C.byref(p), C.byref(n)))
+    return n.value
+
+
+class Batch:
+    """Wrapper of an lbm_batch_t: independent instances in one persistent
+    launch (see include/prc_lbm.h)."""
+
+    def __init__(self, capacity: int, dtype: int, stream_ptr: int = 0):
+        self.dtype = dtype
+        self.b = C.c_void_p()
+        _bcheck(load().lbm_batch_create(capacity, dtype, C.c_void_p(stream_ptr), C.byref(self.b)), None)
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, p: lbm_params, tol: float, max_steps: int) -> int:
+        s = C.c_int()
+        _bcheck(load().lbm_batch_add(self.b, C.byref(p), float(tol), int(max_steps), C.byref(s)), self.b)
+        self.shapes[s.value] = (p.ny, p.nx)
+        return s.value
+
+    def remove(self, slot: int):
+        _bcheck(load().lbm_batch_remove(self.b, slot), self.b)
+        self.shapes.pop(slot, None)
+
+    def launch(self, steps: int, use_graph: bool = True):
+        _bcheck(load().lbm_batch_launch(self.b, int(steps), 1 if use_graph else 0), self.b)
+
+    def wait(self) -> int:
+        n = C.c_int()
+        _bcheck(load().lbm_batch_wait(self.b, C.byref(n)), self.b)
+        return n.value
+
+    def run(self, steps: int, use_graph: bool = True) -> int:
+        self.launch(steps, use_graph)
+        return self.wait()
+
+    def query(self, slot: int):
+        info, st = lbm_info_t(), C.c_int()
+        _bcheck(load().lbm_batch_query(self.b, slot, C.byref(info), C.byref(st)), self.b)
+        return info, st.value
+
+    def fields(self, slot: int):
+        ny, nx = self.shapes[slot]
+        rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+        _bcheck(load().lbm_batch_fields(self.b, slot, _host_ptr(rho), _host_ptr(ux), _host_ptr(uy), 0), self.b)
+        return rho, ux, uy
+
+    def set_populations(self, slot: int, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _bcheck(load().lbm_batch_set_populations(self.b, slot, _host_ptr(f), 0), self.b)
+
+    def populations(self, slot: int):
+        ny, nx = self.shapes[slot]
+        f = np.empty((9, ny, nx))
+        _bcheck(load().lbm_batch_get_populations(self.b, slot, _host_ptr(f), 0), self.b)
+        return f

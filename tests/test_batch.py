@@ -1,0 +1,159 @@
+"""Batched engine: many cavities in one persistent launch.
+
+Every slot of a batch must give exactly what a single-instance handle running
+the same (general) kernel gives, retire at the same step on its own residual,
+be unaffected by the other slots of the mix, and survive a diverging
+neighbour; slots can be added and removed between launches.
+"""
+import numpy as np
+import pytest
+
+from oracle import stepper as S
+from paper_2208_03562_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+L = pytest.importorskip("paper_2208_03562_gb300.lbm")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    L.load()
+
+
+MIX = [
+    # nx, ny, r, gamma, nu, u_lid, bc, drho, fx
+    (70, 19, 2.0, 0.1, 0.01, 0.02, L.BC_CAVITY, L.DRHO_CURRENT, 0.0),
+    (130, 64, 0.5, 0.3, 0.01, 0.03, L.BC_CAVITY, L.DRHO_CURRENT, 0.0),
+    (33, 40, 1.0, 1.0, 0.02, 0.05, L.BC_CHANNEL, L.DRHO_OFF, 1e-5),
+    (96, 32, 0.25, 0.6, 0.002, 0.01, L.BC_PERIODIC, L.DRHO_CURRENT, 2e-6),
+    (5, 7, 1.6, 0.2, 0.005, 0.01, L.BC_CAVITY, L.DRHO_CURRENT, 0.0),
+]
+
+
+def params(case, dtype):
+    nx, ny, r, gamma, nu, u, bc, drho, fx = case
+    return L.lbm_params_init(nx, ny, r, gamma, nu, u, dtype, bc=bc, drho=drho, fx=fx)
+
+
+def start_state(case, seed):
+    nx, ny, r, gamma, nu, u, bc, drho, fx = case
+    w = S.rest_weights(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u))
+    return w[:, None, None] + I.noise(seed, (9, ny, nx), 1e-3)
+
+
+def single(case, dtype, f0):
+    h = L.Lbm(params(case, dtype))
+    h.variant = -1  # the general kernel, as in the batch
+    h.set_populations(f0)
+    return h
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F64, L.F16])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_single_instances(dtype, use_graph):
+    b = L.Batch(8, dtype)
+    slots, refs = [], []
+    for k, case in enumerate(MIX):
+        f0 = start_state(case, 100 + k)
+        s = b.add(params(case, dtype), 0.0, 10 ** 6)
+        b.set_populations(s, f0)
+        slots.append(s)
+        refs.append(single(case, dtype, f0))
+    for n in (7, 40):
+        b.launch(n, use_graph)
+        assert b.wait() == len(MIX)
+        for s, h in zip(slots, refs):
+            h.step(n)
+            info, st = b.query(s)
+            assert st == L.SLOT_ACTIVE and info.step == h.info().step
+            assert np.array_equal(b.populations(s), h.populations())
+            if info.residual_step:
+                assert info.residual == h.residual() and info.mass == h.info().mass
+
+
+def test_each_slot_retires_on_its_own_residual():
+    cav = [I.Cavity(48, 24, 0.5, 0.5, 20.0, 0.02, "f32"), I.Cavity(40, 40, 1.0, 1.0, 50.0, 0.05, "f32"),
+           I.Cavity(30, 60, 2.0, 0.25, 20.0, 0.02, "f32")]
+    tols = [1e-6, 1e-5, 1e-7]
+    b = L.Batch(4, L.F32)
+    slots = [b.add(L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32), t, 500000)
+             for c, t in zip(cav, tols)]
+    active = len(slots)
+    while active:
+        active = b.run(5000)
+    for c, t, s in zip(cav, tols, slots):
+        info, st = b.query(s)
+        assert st == L.SLOT_CONVERGED and info.residual < t
+        h = L.Lbm(L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32))
+        h.variant = -1
+        status, steps = h.run(t, 500000)
+        assert status == L.OK and steps == info.step
+        assert np.array_equal(b.populations(s), h.populations())
+
+
+def test_alone_equals_in_mix():
+    """The same request alone and inside a mix of 40 uneven cavities."""
+    req = I.Cavity(77, 45, 0.5, 0.3, 100.0, 0.03, "f32", 1e-6)
+    mk = lambda c: L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
+    alone = L.Batch(1, L.F32)
+    sa = alone.add(mk(req), req.tol, 40000)
+    while alone.run(2000):
+        pass
+    mix = L.Batch(64, L.F32)
+    others = I.batched_sweep(seed=3, n=40)
+    for c in others[:20]:
+        mix.add(mk(I.Cavity(min(c.nx, 200), min(c.ny, 100), c.r, max(c.gamma, 0.3), c.re, c.u_lid, "f32")),
+                1e-30, 3000)
+    sm = mix.add(mk(req), req.tol, 40000)
+    for c in others[20:]:
+        mix.add(mk(I.Cavity(min(c.nx, 150), min(c.ny, 90), c.r, max(c.gamma, 0.3), c.re, c.u_lid, "f32")),
+                1e-30, 7000)
+    while mix.run(2000):
+        pass
+    ia, sta = alone.query(sa)
+    im, stm = mix.query(sm)
+    assert sta == stm and ia.step == im.step and ia.residual == im.residual
+    assert np.array_equal(alone.populations(sa), mix.populations(sm))
+
+
+def test_diverging_slot_does_not_disturb_the_others():
+    bad = I.deep_cavity_128_as_stated(0.1)
+    good = I.Cavity(64, 32, 0.5, 0.5, 100.0, 0.03, "f32")
+    mk = lambda c: L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
+    b = L.Batch(4, L.F32)
+    sb = b.add(mk(bad), 1e-7, 4000)
+    sg = b.add(mk(good), 1e-30, 1000)
+    b.run(4000)
+    assert b.query(sb)[1] == L.SLOT_DIVERGED
+    info, st = b.query(sg)
+    assert st == L.SLOT_MAXSTEPS and info.step == 1000
+    h = L.Lbm(mk(good))
+    h.variant = -1
+    h.step(1000)
+    assert np.array_equal(b.populations(sg), h.populations())
+
+
+def test_add_and_remove_between_launches():
+    mk = lambda nx, ny: L.lbm_params_init(nx, ny, 1.0, 0.5, 0.02, 0.03, L.F32)
+    b = L.Batch(3, L.F32)
+    s0 = b.add(mk(40, 30), 1e-30, 10 ** 6)
+    s1 = b.add(mk(50, 20), 1e-30, 10 ** 6)
+    b.run(30)
+    b.remove(s0)
+    s2 = b.add(mk(64, 64), 1e-30, 10 ** 6)
+    assert s2 == s0  # the freed slot is reused
+    b.run(30)
+    assert b.query(s1)[0].step == 60 and b.query(s2)[0].step == 30
+    h = L.Lbm(mk(64, 64))
+    h.variant = -1
+    h.step(30)
+    assert np.array_equal(b.populations(s2), h.populations())
+    s3 = b.add(mk(20, 20), 1e-30, 10 ** 6)
+    with pytest.raises(L.LbmError) as e:
+        b.add(mk(20, 20), 1e-30, 10 ** 6)
+    assert e.value.status == L.ENOMEM
+    b.remove(s3)
