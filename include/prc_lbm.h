@@ -289,7 +289,8 @@ typedef enum {
     LBM_SLOT_CONVERGED = 1,
     LBM_SLOT_DIVERGED = 2,
     LBM_SLOT_MAXSTEPS = 3,
-    LBM_SLOT_EMPTY = 4
+    LBM_SLOT_EMPTY = 4,
+    LBM_SLOT_STALLED = 5
 } lbm_slot_state;
 
 lbm_status lbm_batch_create(int capacity, int dtype, void *stream, lbm_batch_t *out);
@@ -299,6 +300,17 @@ lbm_status lbm_batch_instance_bytes(const lbm_params *p, size_t *bytes);
 /* Fill a free slot with an instance at rest; *slot receives its index. */
 lbm_status lbm_batch_add(lbm_batch_t b, const lbm_params *p, double tol, long max_steps, int *slot);
 lbm_status lbm_batch_remove(lbm_batch_t b, int slot);
+/*
+ * Optional stall retirement of a slot (off by default; window = 0 turns it
+ * off).  Every `window` steps of the slot's own counter the residual is
+ * compared with the one recorded `window` steps earlier; if it is above
+ * ratio times that value the slot retires as LBM_SLOT_STALLED.  This detects
+ * the noise floor of a storage format (FP16 keeps 11 significant bits, and
+ * its rounding noise stops the residual of Sec. 5.2 from falling further), so
+ * that a caller can continue the instance in a wider format.  No counterpart
+ * in the paper.  EINVAL for window < 0 or window > 0 with ratio <= 0.
+ */
+lbm_status lbm_batch_set_stall(lbm_batch_t b, int slot, long window, double ratio);
 /* Advance every active slot by up to `steps` steps (one persistent launch). */
 lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph);
 /* Wait for the launch; *n_active receives the slots still active. */

@@ -35,6 +35,8 @@ struct Slot {
     void *mem = nullptr;
     double tol = 0.0;
     long long max_steps = 0;
+    long long stall_window = 0;
+    double stall_ratio = 0.0;
 };
 
 thread_local std::string g_batch_err;
@@ -231,6 +233,8 @@ lbm_status lbm_batch_add(lbm_batch_t b, const lbm_params *p, double tol, long ma
     make_coef(*p, sl.k);
     sl.tol = tol;
     sl.max_steps = max_steps;
+    sl.stall_window = 0;
+    sl.stall_ratio = 0.0;
     cudaError_t e = cudaMallocAsync(&sl.mem, slot_bytes(sl.L), b->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -251,6 +255,19 @@ lbm_status lbm_batch_add(lbm_batch_t b, const lbm_params *p, double tol, long ma
     BCK(b, cudaStreamSynchronize(b->stream));  // the pinned staging buffers are reused
     sl.used = true;
     if (slot) *slot = k;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_stall(lbm_batch_t b, int slot, long window, double ratio)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    s = check_slot(b, slot);
+    if (s != LBM_OK) return s;
+    if (window < 0 || (window > 0 && !(ratio > 0.0))) return bfail(b, LBM_EINVAL, "bad stall window / ratio");
+    Slot &sl = b->slots[slot];
+    sl.stall_window = window;
+    sl.stall_ratio = window > 0 ? ratio : 0.0;
     return LBM_OK;
 }
 
@@ -296,6 +313,8 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         I.force = sl.p.fx != 0.0 || sl.p.fy != 0.0;
         I.tol = sl.tol;
         I.max_steps = sl.max_steps;
+        I.stall_window = sl.stall_window;
+        I.stall_ratio = sl.stall_ratio;
         tiles += I.tiles;
     }
     if (n == 0) return LBM_OK;  // nothing to do

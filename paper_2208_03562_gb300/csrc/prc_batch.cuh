@@ -9,16 +9,27 @@
 // instance reduces that instance's per-tile partial sums in a fixed order,
 // so an instance's result does not depend on the other instances of the mix.
 // An instance retires when its residual falls below its tolerance, when it
-// diverges, or when it reaches its step limit; its tiles are skipped from the
-// next step on.  The grid barrier is a bounded spin: when it runs out it
-// records LBM_ETIMEOUT and every CTA leaves.
+// diverges, when it reaches its step limit, or (optional) when its residual
+// stalls: at the first residual evaluation at least `stall_window` steps after
+// the previous checkpoint, a residual above stall_ratio times the checkpoint's
+// retires the instance as STALLED (a precision floor: the rounding noise of the
+// storage format keeps the residual from falling further).  Its tiles are
+// skipped from the next step on.  The grid barrier is a bounded spin: when it
+// runs out it records LBM_ETIMEOUT and every CTA leaves.
 #pragma once
 
 #include "prc_kernels.cuh"
 
 namespace prc {
 
-enum BatchState : int { BATCH_ACTIVE = 0, BATCH_CONVERGED = 1, BATCH_DIVERGED = 2, BATCH_MAXSTEPS = 3, BATCH_EMPTY = 4 };
+enum BatchState : int {
+    BATCH_ACTIVE = 0,
+    BATCH_CONVERGED = 1,
+    BATCH_DIVERGED = 2,
+    BATCH_MAXSTEPS = 3,
+    BATCH_EMPTY = 4,
+    BATCH_STALLED = 5
+};
 
 // Read-only part of an instance descriptor (set by the host before a launch).
 struct BatchInst {
@@ -33,6 +44,8 @@ struct BatchInst {
     int drho, force;
     double tol;
     long long max_steps;
+    long long stall_window;  // steps between stall checkpoints (0: no stall test)
+    double stall_ratio;      // stalled when res > stall_ratio * checkpoint residual
 };
 
 // Mutable part, updated on the device.
@@ -42,6 +55,8 @@ struct BatchDyn {
     double res, mass;
     int state;
     int pad;
+    long long chk_step;  // stall checkpoint: step and residual
+    double chk_res;
 };
 
 struct BatchCtl {
@@ -153,12 +168,24 @@ k_batch(const BatchInst *__restrict__ inst, const Coef<T> *__restrict__ coefs, B
             batch_tile<S, T>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start, epi, partials);
         }
         if (!grid_barrier(ctl)) return;
-        // ---- bookkeeping: counters, residuals, retirement (one CTA per instance)
+        // ---- bookkeeping: counters, residuals, retirement (one CTA per instance).
+        // Thread 0 reads the instance's state and counter once into shared
+        // memory and is the only writer; the barriers keep every branch below
+        // uniform across the CTA (a thread that re-read D->t after thread 0
+        // advanced it would take a different branch).
+        __shared__ long long sh_t;
+        __shared__ int sh_active;
         for (int j = blockIdx.x; j < ninst; j += gridDim.x) {
             const BatchInst &I = inst[j];
             BatchDyn *D = dyn + I.slot;
-            if (ld_relaxed_i32(&D->state) != BATCH_ACTIVE) continue;
-            const long long t = __ldcg(&D->t) + 1;
+            __syncthreads();  // the previous instance's shared values are consumed
+            if (tid == 0) {
+                sh_active = ld_relaxed_i32(&D->state) == BATCH_ACTIVE;
+                sh_t = __ldcg(&D->t) + 1;
+            }
+            __syncthreads();
+            if (!sh_active) continue;
+            const long long t = sh_t;
             if (t % 20 == 0) {
                 __shared__ double sa[BX * BY], sb[BX * BY];
                 double a = 0.0, b = 0.0;
@@ -184,6 +211,11 @@ k_batch(const BatchInst *__restrict__ inst, const Coef<T> *__restrict__ coefs, B
                     D->res_step = t;
                     if (!isfinite(res) || !isfinite(mass)) D->state = BATCH_DIVERGED;
                     else if (res < I.tol) D->state = BATCH_CONVERGED;
+                    else if (I.stall_window > 0 && t - D->chk_step >= I.stall_window) {
+                        if (D->chk_step > 0 && res > I.stall_ratio * D->chk_res) D->state = BATCH_STALLED;
+                        D->chk_step = t;
+                        D->chk_res = res;
+                    }
                 }
                 __syncthreads();
             }

@@ -91,6 +91,7 @@ def load():
         "lbm_batch_instance_bytes": [P, C.POINTER(C.c_size_t)],
         "lbm_batch_add": [B, P, C.c_double, C.c_long, C.POINTER(C.c_int)],
         "lbm_batch_remove": [B, C.c_int],
+        "lbm_batch_set_stall": [B, C.c_int, C.c_long, C.c_double],
         "lbm_batch_launch": [B, C.c_long, C.c_int],
         "lbm_batch_wait": [B, C.POINTER(C.c_int)],
         "lbm_batch_run": [B, C.c_long, C.POINTER(C.c_int)],
@@ -126,7 +127,7 @@ def exported_symbols():
                  "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
                  "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc", "lbm_batch_create",
                  "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_instance_bytes", "lbm_batch_add",
-                 "lbm_batch_remove", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
+                 "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
                  "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations"):
         if hasattr(L, name):
             out.append(name)
@@ -411,8 +412,8 @@ class Lbm:
 # ---------------------------------------------------------------------------
 # batched engine
 
-SLOT_ACTIVE, SLOT_CONVERGED, SLOT_DIVERGED, SLOT_MAXSTEPS, SLOT_EMPTY = range(5)
-SLOT_NAMES = ["ACTIVE", "CONVERGED", "DIVERGED", "MAXSTEPS", "EMPTY"]
+SLOT_ACTIVE, SLOT_CONVERGED, SLOT_DIVERGED, SLOT_MAXSTEPS, SLOT_EMPTY, SLOT_STALLED = range(6)
+SLOT_NAMES = ["ACTIVE", "CONVERGED", "DIVERGED", "MAXSTEPS", "EMPTY", "STALLED"]
 
 
 def _bcheck(status, b):
@@ -459,6 +460,11 @@ class Batch:
         _bcheck(load().lbm_batch_remove(self.b, slot), self.b)
         self.shapes.pop(slot, None)
 
+    def set_stall(self, slot: int, window: int, ratio: float):
+        """Retire the slot as STALLED when its residual stops falling (see
+        lbm_batch_set_stall); window = 0 turns the test off."""
+        _bcheck(load().lbm_batch_set_stall(self.b, slot, int(window), float(ratio)), self.b)
+
     def launch(self, steps: int, use_graph: bool = True):
         _bcheck(load().lbm_batch_launch(self.b, int(steps), 1 if use_graph else 0), self.b)
 
@@ -491,3 +497,11 @@ class Batch:
         f = np.empty((9, ny, nx))
         _bcheck(load().lbm_batch_get_populations(self.b, slot, _host_ptr(f), 0), self.b)
         return f
+
+    def populations_to_device(self, slot: int, f_ptr: int):
+        """Full FP64 populations of a slot into a device buffer of 9 ny nx doubles."""
+        _bcheck(load().lbm_batch_get_populations(self.b, slot, C.c_void_p(f_ptr), 1), self.b)
+
+    def set_populations_from_device(self, slot: int, f_ptr: int):
+        """Set a slot from a device buffer of 9 ny nx FP64 full populations."""
+        _bcheck(load().lbm_batch_set_populations(self.b, slot, C.c_void_p(f_ptr), 1), self.b)

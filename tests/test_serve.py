@@ -1,0 +1,244 @@
+"""Continuous-batching solve server (paper_2208_03562_gb300.serve).
+
+CPU tests drive the scheduler with a fake batch whose residual decays
+deterministically to a precision floor. They check:
+- admission by memory and slots;
+- first-come-first-served order;
+- rejection of requests that can never fit;
+- promotion of stalled slots;
+- latency accounting.
+
+The GPU tests run the real engine. They check that a solve gives bitwise the
+same result alone and inside a mix of requests that arrive while it runs, and
+that the FP16 -> FP32 schedule ends within tolerance of the FP64 oracle.
+"""
+import math
+import types
+
+import numpy as np
+import pytest
+
+from paper_2208_03562_gb300 import serve as SV
+
+F64, F32, F16 = 0, 1, 2
+FLOOR = {F16: 3e-5, F32: 1e-10, F64: 1e-14}
+
+
+class FakeParams:
+    _fields_ = [("nx", None), ("ny", None), ("r", None), ("gamma", None), ("nu", None), ("u_lid", None),
+                ("dtype", None)]
+
+    def __init__(self, nx=0, ny=0, r=1.0, gamma=1.0, nu=0.05, u_lid=0.05, dtype=F32):
+        self.nx, self.ny, self.r, self.gamma, self.nu, self.u_lid, self.dtype = nx, ny, r, gamma, nu, u_lid, dtype
+
+
+def fake_bytes(p, dtype):
+    return 2 * 9 * p.nx * p.ny * {F64: 8, F32: 4, F16: 2}[dtype]
+
+
+class FakeWorld:
+    """A shared virtual clock, device memory for staging, and all fake batches."""
+
+    def __init__(self, glups=1.0):
+        self.t = 0.0
+        self.glups = glups
+        self.staged = {}
+        self.batches = []
+
+    def clock(self):
+        return self.t
+
+    def sleep(self, s):
+        self.t += s
+
+    def staging(self, n):
+        return 1234  # one fake device pointer
+
+    def make_batch(self, capacity, dtype):
+        b = FakeBatch(self, capacity, dtype)
+        self.batches.append(b)
+        return b
+
+
+class FakeBatch:
+    """Residual of a slot at its own step t (evaluated every 20 steps):
+    exp(-(t + t_offset) / tau) + floor(dtype), tau = 50 nx ny / 1000.
+    A promoted slot carries t_offset over."""
+
+    def __init__(self, world, capacity, dtype):
+        self.w, self.capacity, self.dtype = world, capacity, dtype
+        self.slots = {}
+        self.in_flight = False
+        self.max_used_slots = 0
+
+    def add(self, p, tol, max_steps):
+        free = [i for i in range(self.capacity) if i not in self.slots]
+        assert free, "no free slot"
+        s = free[0]
+        self.slots[s] = types.SimpleNamespace(p=p, tol=tol, max_steps=max_steps, t=0, off=0, res=math.inf,
+                                              res_step=0, state=SV.SLOT_ACTIVE, window=0, ratio=0.0,
+                                              chk_step=0, chk_res=0.0)
+        self.max_used_slots = max(self.max_used_slots, len(self.slots))
+        return s
+
+    def set_stall(self, slot, window, ratio):
+        self.slots[slot].window, self.slots[slot].ratio = window, ratio
+
+    def remove(self, slot):
+        del self.slots[slot]
+
+    def _res(self, sl, t):
+        tau = 50.0 * sl.p.nx * sl.p.ny / 1000.0
+        return math.exp(-(t + sl.off) / tau) + FLOOR[self.dtype]
+
+    def launch(self, steps):
+        assert not self.in_flight
+        self.in_flight = True
+        work = 0
+        for sl in self.slots.values():
+            if sl.state != SV.SLOT_ACTIVE:
+                continue
+            for _ in range(steps):
+                sl.t += 1
+                work += sl.p.nx * sl.p.ny
+                if sl.t % 20 == 0:
+                    sl.res, sl.res_step = self._res(sl, sl.t), sl.t
+                    if sl.res < sl.tol:
+                        sl.state = SV.SLOT_CONVERGED
+                    elif sl.window > 0 and sl.t - sl.chk_step >= sl.window:
+                        if sl.chk_step > 0 and sl.res > sl.ratio * sl.chk_res:
+                            sl.state = SV.SLOT_STALLED
+                        sl.chk_step, sl.chk_res = sl.t, sl.res
+                if sl.state == SV.SLOT_ACTIVE and sl.t >= sl.max_steps:
+                    sl.state = SV.SLOT_MAXSTEPS
+                if sl.state != SV.SLOT_ACTIVE:
+                    break
+        self.w.t += work / (self.w.glups * 1e9) + 1e-4
+
+    def wait(self):
+        self.in_flight = False
+        return sum(1 for s in self.slots.values() if s.state == SV.SLOT_ACTIVE)
+
+    def query(self, slot):
+        sl = self.slots[slot]
+        return types.SimpleNamespace(step=sl.t, residual=sl.res, residual_step=sl.res_step), sl.state
+
+    def fields(self, slot):
+        sl = self.slots[slot]
+        return (np.full((sl.p.ny, sl.p.nx), float(sl.t + sl.off)),)
+
+    def populations_to_device(self, slot, ptr):
+        self.w.staged[ptr] = self.slots[slot].t + self.slots[slot].off
+
+    def set_populations_from_device(self, slot, ptr):
+        sl = self.slots[slot]
+        sl.off, sl.t, sl.state, sl.res = self.w.staged[ptr], 0, SV.SLOT_ACTIVE, math.inf
+
+    def close(self):
+        pass
+
+
+def make_server(world, stages, capacity=4, budget=10 ** 9, **kw):
+    return SV.SolveServer(stages, capacity, budget, world.make_batch, fake_bytes, world.staging,
+                          clock=world.clock, sleep=world.sleep, **kw)
+
+
+def reqs(shapes, tol=1e-6, gap=0.01, max_steps=10 ** 6):
+    return [SV.SolveRequest(i, i * gap, FakeParams(nx, ny), tol, max_steps) for i, (nx, ny) in enumerate(shapes)]
+
+
+def test_every_request_converges_in_one_stage():
+    w = FakeWorld()
+    srv = make_server(w, [SV.Stage(F32)])
+    res = srv.serve(reqs([(64, 32), (128, 64), (100, 100)]))
+    assert sorted(r.rid for r in res) == [0, 1, 2]
+    assert all(r.status == "converged" and r.residual < 1e-6 and r.steps % 20 == 0 for r in res)
+    assert all(r.done_s >= r.admit_s >= r.arrival_s for r in res)
+    assert srv.used == 0 and not srv.live
+
+
+def test_admission_respects_memory_budget_and_fifo():
+    w = FakeWorld()
+    shapes = [(200, 100)] * 6
+    one = fake_bytes(FakeParams(200, 100), F32)
+    srv = make_server(w, [SV.Stage(F32)], capacity=8, budget=2 * one + one // 2)
+    seen = []
+    orig = srv._admit
+
+    def spy(req, now):
+        ok = orig(req, now)
+        seen.append((req.rid, ok, srv.used))
+        return ok
+    srv._admit = spy
+    res = srv.serve(reqs(shapes, gap=0.0))
+    assert max(u for _, _, u in seen) <= srv.budget
+    assert w.batches[0].max_used_slots == 2  # memory, not the 8 slots, limits the mix
+    admitted = [rid for rid, ok, _ in seen if ok]
+    assert admitted == sorted(admitted)  # first come, first served
+    assert all(r.status == "converged" for r in res)
+    waits = sorted(r.queue_s for r in res)
+    assert waits[0] == 0.0 and waits[-1] > 0.0
+
+
+def test_slot_capacity_limits_the_mix():
+    w = FakeWorld()
+    srv = make_server(w, [SV.Stage(F32)], capacity=2)
+    srv.serve(reqs([(32, 32)] * 5, gap=0.0))
+    assert w.batches[0].max_used_slots == 2
+    assert len(srv.results) == 5
+
+
+def test_request_that_never_fits_is_rejected_not_blocking():
+    w = FakeWorld()
+    srv = make_server(w, [SV.Stage(F32)], budget=fake_bytes(FakeParams(100, 100), F32))
+    res = srv.serve(reqs([(1000, 1000), (50, 50)], gap=0.0))
+    st = {r.rid: r.status for r in res}
+    assert st == {0: "rejected", 1: "converged"}
+
+
+def test_fp16_stall_promotes_to_fp32():
+    w = FakeWorld()
+    stages = [SV.Stage(F16, stall_window=400, stall_ratio=0.9), SV.Stage(F32)]
+    srv = make_server(w, stages)
+    res = srv.serve(reqs([(64, 32), (96, 48)], tol=1e-6))
+    for r in res:
+        assert r.status == "converged" and len(r.steps_by_stage) == 2 and r.residual < 1e-6
+        # the FP32 stage resumed where FP16 stopped: total progress is continuous
+        assert r.fields[0][0, 0] == r.steps
+    assert srv.used == srv.staging_bytes
+
+
+def test_fp16_alone_reaches_tol_without_promotion():
+    w = FakeWorld()
+    stages = [SV.Stage(F16, stall_window=400), SV.Stage(F32)]
+    srv = make_server(w, stages)
+    res = srv.serve(reqs([(64, 32)], tol=1e-3))
+    assert res[0].status == "converged" and len(res[0].steps_by_stage) == 1
+
+
+def test_result_same_alone_and_in_mix_fake():
+    base = SV.SolveRequest(0, 0.05, FakeParams(80, 40), 1e-6, 10 ** 6)
+    stages = [SV.Stage(F16, stall_window=400, stall_ratio=0.9), SV.Stage(F32)]
+    w1 = FakeWorld()
+    alone = make_server(w1, stages).serve([base])[0]
+    w2 = FakeWorld()
+    others = reqs([(64, 64), (128, 32), (50, 70), (90, 90)], gap=0.02)
+    for o in others:
+        o.rid += 1
+    mix = {r.rid: r for r in make_server(w2, stages).serve([base] + others)}
+    assert mix[0].steps == alone.steps and mix[0].steps_by_stage == alone.steps_by_stage
+    assert mix[0].residual == alone.residual
+
+
+def test_chunk_follows_the_resident_work():
+    w = FakeWorld()
+    srv = make_server(w, [SV.Stage(F32)], chunk_node_steps=1e6, max_chunk=5000)
+    assert srv.chunk_steps() == 5000  # nothing resident
+    srv._admit(reqs([(1000, 1000)])[0], 0.0)
+    assert srv.chunk_steps() == 20
+
+
+def test_percentile_nearest_rank():
+    xs = list(range(1, 101))
+    assert SV.percentile(xs, 50) == 50 and SV.percentile(xs, 99) == 99 and SV.percentile(xs, 100) == 100
+    assert math.isnan(SV.percentile([], 50))
