@@ -37,8 +37,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-extras", action="store_true", help="skip FP16, e2e and CPU-baseline legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip every leg but the primary one")
+    ap.add_argument("--skip", default="", help="comma-separated legs to skip: time_to_steady_state, "
+                                               "batched_sweep, serving")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "f64"], help="storage of the primary leg")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="profiling only: use this interior-kernel variant instead of autotuning")
     ap.add_argument("--nx", type=int, default=0, help="profiling only: override the grid width")
     ap.add_argument("--ny", type=int, default=0, help="profiling only: override the grid height")
     return ap.parse_args()
@@ -142,6 +146,7 @@ class ClockSampler:
 
 
 GRID_OVERRIDE = {}
+FORCE_VARIANT = {}
 
 
 def workload(dtype):
@@ -168,7 +173,11 @@ def gpu_leg(cav_dtype, steps, warmup, torch, L, dist=None, clocks_index=None):
     p = L.lbm_params_init(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.DTYPE_CODES[cav_dtype])
     g = L.Lbm(p, torch_workspace=True)
     from paper_2208_03562_gb300 import autotune
-    tuned = autotune.tune(g, steps=20)
+    if FORCE_VARIANT and cav_dtype in FORCE_VARIANT:
+        g.variant = FORCE_VARIANT[cav_dtype]
+        tuned = {"variant": g.variant, "forced": True}
+    else:
+        tuned = autotune.tune(g, steps=20)
     tuned["shapes"] = [L.lbm_variant_info(p.dtype, i) for i in range(L.lbm_variant_count(p.dtype))]
     stream = torch.cuda.current_stream()
     g.step(warmup)
@@ -193,8 +202,31 @@ def gpu_leg(cav_dtype, steps, warmup, torch, L, dist=None, clocks_index=None):
         ms = float(t.item())
         dist.barrier()
     info = g.info()
+    launch = launch_times(g, min(steps, 200), torch)
     g.close()
-    return cav, ms, info, (sampler.summary() if sampler else None), tuned
+    return cav, ms, info, (sampler.summary() if sampler else None), tuned, launch
+
+
+def launch_times(g, n, torch):
+    """Duration of each step launch, from CUDA events recorded on the stream
+    the step kernel is launched on (the handle enqueues on PyTorch's current
+    stream), one step per lbm_step call (no graph).  A step is one launch of
+    the fused step kernel; every 20th step also launches the residual
+    finalisation, so those are reported apart."""
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    t_first = g.info().step
+    for a, b in ev:
+        a.record(stream)
+        g.step(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    plain, epi = [], []
+    for k, (a, b) in enumerate(ev):
+        ((epi if (t_first + k + 1) % 20 == 0 else plain)).append(a.elapsed_time(b))
+    mean = lambda xs: sum(xs) / len(xs) if xs else None
+    return {"launches": n, "ms_step_kernel": mean(plain), "ms_residual_step": mean(epi),
+            "n_plain": len(plain), "n_residual": len(epi)}
 
 
 def e2e_leg(steps, torch, L):
@@ -224,6 +256,105 @@ def e2e_leg(steps, torch, L):
             "h2d_bytes_per_step": 3 * 8 * n / steps, "d2h_bytes_per_step": 3 * 8 * n / steps,
             "wall_s": dt, "what": "lbm_init_fields(host, pinned) + lbm_step(%d) + lbm_fields(host, pinned); "
                                   "bytes per step are the per-solve transfers divided by the steps" % steps}
+
+
+def ttss_leg(L, budget_s=150.0):
+    """Time to steady state on the deep cavity (128 x 128, r = 2, Re = 1000,
+    Ma = 0.06): the preconditioned FP32 path (gamma = 0.1) and the plain FP64
+    path (gamma = 1, no preconditioning), both single-instance handles run to
+    residual 1e-6 (Sec. 5.2), wall time from the first step to the step that
+    met the residual, with the residual checks included."""
+    from paper_2208_03562_gb300 import inputs as I
+    import time as _t
+    out = {"workload": "deep lid-driven cavity 128x128, r=2 (H/L=2), Re=1000, Ma=0.06, from rest",
+           "tol": 1e-6}
+    for name, dt, gamma, bud in (("f32_gamma0.1", L.F32, 0.1, budget_s / 3),
+                                 ("f16_to_f32_gamma0.1", None, 0.1, budget_s / 3),
+                                 ("f64_plain_gamma1", L.F64, 1.0, budget_s)):
+        cav = I.deep_cavity_128(gamma)
+        t0 = _t.perf_counter()
+        steps, st = 0, None
+        if dt is None:  # FP16 storage until the residual stalls, then FP32
+            from paper_2208_03562_gb300 import serve as SV
+            srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=2, reserve_bytes=0, budget_bytes=1 << 30,
+                                keep_fields=False)
+            p = L.lbm_params_init(cav.nx, cav.ny, cav.r, gamma, cav.nu, cav.u_lid, L.F16)
+            r = srv.serve([SV.SolveRequest(0, 0.0, p, 1e-6, 20_000_000)], time_limit_s=bud)
+            srv.close()
+            dts = _t.perf_counter() - t0
+            if r:
+                out[name] = {"status": r[0].status, "steps": r[0].steps, "steps_by_stage": r[0].steps_by_stage,
+                             "s": dts, "residual": r[0].residual}
+            else:
+                out[name] = {"status": "unfinished", "s": dts}
+            continue
+        p = L.lbm_params_init(cav.nx, cav.ny, cav.r, gamma, cav.nu, cav.u_lid, dt)
+        g = L.Lbm(p)
+        while _t.perf_counter() - t0 < bud:
+            st, n = g.run(1e-6, 100000)
+            steps += n
+            if st == L.OK:
+                break
+        dts = _t.perf_counter() - t0
+        out[name] = {"status": "converged" if st == L.OK else "unfinished", "steps": steps, "s": dts,
+                     "residual": g.residual(), "us_per_step": 1e6 * dts / max(steps, 1)}
+        g.close()
+    a, b = out.get("f32_gamma0.1", {}), out.get("f64_plain_gamma1", {})
+    if a.get("status") == "converged" and b.get("status") == "converged":
+        out["speedup_f32_vs_f64_plain"] = b["s"] / a["s"]
+        out["step_ratio_gamma1_over_gamma0.1"] = b["steps"] / a["steps"]
+    return out
+
+
+def batch_leg(L, budget_s=30.0, n=256):
+    """The batched sweep: n uneven cavities (seed 0) in one batch, persistent
+    launches until every slot retired or the time budget ran out; aggregate
+    GLUPS over the slots' own steps."""
+    from paper_2208_03562_gb300 import inputs as I
+    import time as _t
+    cavs = I.batched_sweep(seed=0, n=n, dtype="f32")
+    b = L.Batch(n, L.F32)
+    slots = []
+    for c in cavs:
+        p = L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
+        slots.append((b.add(p, c.tol, c.max_steps), c.nodes))
+    t0 = _t.perf_counter()
+    launches, active = 0, n
+    while active and _t.perf_counter() - t0 < budget_s:
+        active = b.run(2000)
+        launches += 1
+    dt = _t.perf_counter() - t0
+    ns, states = 0, {}
+    for s, nodes in slots:
+        info, st = b.query(s)
+        ns += info.step * nodes
+        states[L.SLOT_NAMES[st]] = states.get(L.SLOT_NAMES[st], 0) + 1
+    b.close()
+    return {"workload": "%d cavities, nx 64..1024, ny 32..512, r in {0.25,0.5,1,2}, gamma 0.05..1, Re 100..5000, "
+                        "FP32, residual 1e-7 (seed 0)" % n,
+            "aggregate_glups": ns / dt / 1e9, "wall_s": dt, "launches": launches, "states": states,
+            "note": "time-bounded: slots still ACTIVE had not reached 1e-7 when the budget ran out"}
+
+
+def serve_leg(L, budget_s=40.0, n=256):
+    """The serving workload: Poisson arrivals (50/s, seed 0) of steady-state
+    solves, FP16 storage until the residual stalls, then FP32 to 1e-6."""
+    from paper_2208_03562_gb300 import inputs as I
+    from paper_2208_03562_gb300 import serve as SV
+    reqs = []
+    for i, rq in enumerate(I.serving_requests(seed=0, n=n)):
+        c = rq.cavity
+        reqs.append(SV.SolveRequest(i, rq.arrival_s, L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid,
+                                                                        L.F16), c.tol, c.max_steps))
+    srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=n, keep_fields=False)
+    res = srv.serve(reqs, time_limit_s=budget_s)
+    sm = SV.summary(srv, res)
+    srv.close()
+    sm["unfinished"] = n - len(res)
+    sm["workload"] = ("%d requests, Poisson 50/s, nx 128..2048, ny 64..1024, r 0.25..2, gamma 0.05..1, "
+                      "Re 100..1000, FP16->FP32, residual 1e-6 (seed 0)" % n)
+    sm["note"] = "time-bounded: percentiles are over the requests that finished within the budget"
+    return sm
 
 
 def oracle_sample_rate(nx, ny, steps_budget_s=12.0, max_steps=200):
@@ -274,6 +405,8 @@ def main():
     args = parse()
     if args.nx or args.ny:
         GRID_OVERRIDE.update(nx=args.nx, ny=args.ny)
+    if args.variant is not None:
+        FORCE_VARIANT[args.dtype] = args.variant
     if args.impl == "reference":
         return reference_main(args)
     import torch
@@ -289,38 +422,55 @@ def main():
     dev_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES") else local
 
-    cav, ms, info, clocks, tuned = gpu_leg(args.dtype, args.steps, args.warmup, torch, L, dist, dev_index)
+    cav, ms, info, clocks, tuned, launch = gpu_leg(args.dtype, args.steps, args.warmup, torch, L, dist, dev_index)
     nodes = cav.nodes
     ms_step = ms / args.steps
     glups = world * nodes * args.steps / (ms / 1e3) / 1e9
     peak, peak_kind = peak_hbm()
     bpn = BYTES_PER_NODE[args.dtype]
-    achieved = bpn * nodes / (ms_step / 1e3) / 1e9
+    achieved = bpn * nodes / (launch["ms_step_kernel"] / 1e3) / 1e9
     line = {"metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": config_of(cav),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": ncu_traffic("k_step_" + args.dtype),
-                         "peak_kind": peak_kind, "bytes_per_node": bpn,
-                         "kernel": "k_step (+ 1 finalize per 20 steps in the timed region)"},
-            "gpu_launches": 1 + args.steps + args.steps // 20,
+                         "peak_kind": peak_kind, "bytes_per_node": bpn, "nodes_per_launch": nodes,
+                         "kernel": "k_step_tma (interior tiles + edge strips, one launch per step)",
+                         "timing": launch},
+            "gpu_launches": args.steps + args.steps // 20,
             "clocks": clocks,
             "residual_at_end": info.residual,
             "autotune": tuned}
     if not args.no_extras and args.dtype == "f32":
-        cav16, ms16, _, _, tuned16 = gpu_leg("f16", args.steps, args.warmup, torch, L, dist, None)
+        cav16, ms16, _, _, tuned16, launch16 = gpu_leg("f16", args.steps, args.warmup, torch, L, dist, None)
         s16 = ms16 / args.steps
-        a16 = BYTES_PER_NODE["f16"] * nodes / (s16 / 1e3) / 1e9
+        a16 = BYTES_PER_NODE["f16"] * nodes / (launch16["ms_step_kernel"] / 1e3) / 1e9
         line["fp16"] = {"value": world * nodes * args.steps / (ms16 / 1e3) / 1e9, "unit": "GLUPS",
                         "ms_per_step": s16, "roofline": {"achieved": a16, "peak": peak, "frac": a16 / peak,
                                                          "bytes_per_node": 36,
-                                                         "traffic": ncu_traffic("k_step_f16")},
+                                                         "traffic": ncu_traffic("k_step_f16"),
+                                                         "timing": launch16},
                         "autotune": tuned16}
+    if not args.no_extras and args.dtype == "f32":
+        cav64, ms64, _, _, _, launch64 = gpu_leg("f64", max(20, args.steps // 10), args.warmup, torch, L, dist, None)
+        st64 = max(20, args.steps // 10)
+        line["fp64"] = {"value": world * nodes * st64 / (ms64 / 1e3) / 1e9, "unit": "GLUPS",
+                        "ms_per_step": ms64 / st64, "steps": st64,
+                        "roofline_hbm": {"achieved": 144 * nodes / (launch64["ms_step_kernel"] / 1e3) / 1e9,
+                                         "peak": peak, "bytes_per_node": 144},
+                        "note": "plain FP64 path (general kernel, FP64 collision): bound by FP64 ALU throughput"}
     if rank == 0 and not args.no_extras:
         try:
             line["e2e"] = e2e_leg(args.steps, torch, L)
         except Exception as e:  # reported, not hidden
             line["e2e"] = {"error": repr(e)}
+        for key, fn in (("time_to_steady_state", ttss_leg), ("batched_sweep", batch_leg), ("serving", serve_leg)):
+            if key in args.skip:
+                continue
+            try:
+                line[key] = fn(L)
+            except Exception as e:  # reported, not hidden
+                line[key] = {"error": repr(e)}
         v, threads, steps, dt = oracle_sample_rate(8192, 64)
         line["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": threads, "kind": "oracle",
                                 "sample": "FP64 oracle on an 8192x64 slab of the workload, %d steps, %.1f s"

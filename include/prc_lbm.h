@@ -165,6 +165,18 @@ lbm_status lbm_residual(lbm_t h, double *res);
 /* Synchronise and return the total mass sum rho of the current state, FP64. */
 lbm_status lbm_mass(lbm_t h, double *mass);
 
+/*
+ * Set the total mass sum rho to `mass` by a uniform density shift
+ * f~_i += w_i(r) delta at every node (w_i(r): the rest populations, which
+ * carry density and no momentum).  The method conserves mass exactly in a
+ * closed domain (App. A: k~00 = k00, and bounce-back returns every
+ * population); reduced-precision storage does not, because every stored
+ * population is rounded.  A caller that moves a state from FP16 to wider
+ * storage uses this to restore the invariant.  Synchronises.  EINVAL for a
+ * mass that is not finite and positive.
+ */
+lbm_status lbm_set_mass(lbm_t h, double mass);
+
 /* Synchronise and fill the progress record. */
 lbm_status lbm_info(lbm_t h, lbm_info_t *info);
 
@@ -208,18 +220,30 @@ lbm_status lbm_save(lbm_t h, void *host_buf, size_t n);
 lbm_status lbm_load(lbm_t h, const void *host_buf, size_t n);
 
 /*
- * Interior-kernel variants.  Nodes at least two lattice spacings from every
- * wall are updated by a TMA-staged persistent kernel compiled in a few tile
- * shapes; the rest by the general wall-aware kernel.  These calls list the
- * compiled variants of a storage type, select one for a handle (-1 = the
- * general kernel everywhere; results agree to round-off), and time every
- * variant on the handle's own grid.  lbm_autotune runs `steps` plain steps
- * per variant (rounded up to even), then restores the populations, the
- * residual snapshot, the status and the step counter exactly, selects the
- * fastest variant and returns its index in *best and the per-variant
- * milliseconds per step in ms_per_step[0..n) (either may be NULL).
+ * Kernel variants.  Nodes at least two lattice spacings from every wall are
+ * updated by a TMA-staged persistent kernel compiled in a few tile shapes
+ * (variants 0 .. n-1); the edge strips ride in the same launch.  Variant -1
+ * is the general wall-aware kernel everywhere.  Variant LBM_VARIANT_CLUSTER
+ * (-2) is the cluster-resident engine for small grids: one thread-block
+ * cluster of up to 16 CTAs keeps the whole state in distributed shared
+ * memory and advances it many steps per launch (a slab of rows per CTA,
+ * cluster barriers between steps); it needs every slab of >= 2 rows to fit
+ * the shared memory of a CTA (e.g. up to about 50 000 nodes in FP32), and is
+ * the default of lbm_create when it fits.  All variants give the same
+ * populations up to round-off; the cluster engine and the general kernel
+ * give bitwise the same populations.
+ * lbm_variant_count / _info list the interior variants of a storage type;
+ * lbm_set_variant selects one for a handle (EINVAL when the cluster engine
+ * does not fit the grid).  lbm_autotune times every candidate on the
+ * handle's own grid: `steps` plain steps each (rounded up to even), then
+ * restores the populations, the residual snapshot, the status and the step
+ * counter exactly, selects the fastest and returns it in *best;
+ * ms_per_step[0..n) receives the milliseconds per step of the interior
+ * variants and ms_per_step[n] that of the cluster engine (-1 when it does
+ * not fit), so the array holds n + 1 values.  Either pointer may be NULL.
  * No counterpart in the paper: these choose how the same update is executed.
  */
+#define LBM_VARIANT_CLUSTER (-2)
 lbm_status lbm_variant_count(int dtype, int *n);
 lbm_status lbm_variant_info(int dtype, int variant, int *tile_w, int *tile_h, int *threads, int *ctas_per_sm);
 lbm_status lbm_get_variant(lbm_t h, int *variant);
@@ -325,6 +349,10 @@ lbm_status lbm_batch_query(lbm_batch_t b, int slot, lbm_info_t *info, int *state
 lbm_status lbm_batch_fields(lbm_batch_t b, int slot, double *rho, double *ux, double *uy, int on_device);
 lbm_status lbm_batch_set_populations(lbm_batch_t b, int slot, const double *f, int on_device);
 lbm_status lbm_batch_get_populations(lbm_batch_t b, int slot, double *f, int on_device);
+/* Total mass of a slot's current state (FP64), and the density shift of
+ * lbm_set_mass applied to a slot. */
+lbm_status lbm_batch_mass(lbm_batch_t b, int slot, double *mass);
+lbm_status lbm_batch_set_mass(lbm_batch_t b, int slot, double mass);
 
 /* Derived constants: shear relaxation rate omega_nu and q = min(1, r). */
 lbm_status lbm_omega_nu(const lbm_params *p, double *omega_nu);

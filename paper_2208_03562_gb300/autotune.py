@@ -62,14 +62,15 @@ def _store(d):
 
 def tune(lb: "L.Lbm", steps: int = 20, use_cache: bool = True) -> dict:
     """Select the variant for ``lb``; returns {"variant", "ms_per_step", "cached"}."""
-    if L.lbm_variant_count(lb.p.dtype) == 0:
-        return {"variant": -1, "ms_per_step": [], "cached": False}
     k = key_of(lb.p)
     with _LOCK:
         d = _load() if use_cache else {}
         if k in d:
-            lb.variant = d[k]["variant"]
-            return {"variant": d[k]["variant"], "ms_per_step": d[k]["ms_per_step"], "cached": True}
+            try:
+                lb.variant = d[k]["variant"]
+                return {"variant": d[k]["variant"], "ms_per_step": d[k]["ms_per_step"], "cached": True}
+            except L.LbmError:
+                pass  # e.g. the cluster engine does not fit this grid of the bucket: re-tune
         best, ms = lb.autotune(steps)
         d = _load()
         d[k] = {"variant": best, "ms_per_step": ms}

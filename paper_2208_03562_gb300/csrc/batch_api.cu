@@ -465,6 +465,44 @@ lbm_status lbm_batch_set_populations(lbm_batch_t b, int slot, const double *f, i
     return LBM_OK;
 }
 
+lbm_status lbm_batch_mass(lbm_batch_t b, int slot, double *mass)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    s = check_slot(b, slot);
+    if (s != LBM_OK) return s;
+    if (!mass) return bfail(b, LBM_EINVAL, "null out");
+    const Slot &sl = b->slots[slot];
+    const dim3 g = prc::step_grid(sl.gd);
+    const size_t np = (size_t)g.x * g.y;
+    void *tmp = nullptr;
+    BCK(b, cudaMallocAsync(&tmp, np * sizeof(double2), b->stream));
+    std::vector<double2> h(np);
+    cudaError_t e = b->ops->mass_partial(slot_pop(sl, (int)(b->h_dyn[slot].t & 1)), sl.gd,
+                                         static_cast<double2 *>(tmp), b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), tmp, np * sizeof(double2), cudaMemcpyDeviceToHost, b->stream);
+    cudaFreeAsync(tmp, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("mass: ") + cudaGetErrorString(e));
+    double m = 0.0;
+    for (size_t i = 0; i < np; i++) m += h[i].y;  // fixed order
+    *mass = (double)sl.p.nx * (double)sl.p.ny + m;
+    return std::isfinite(*mass) ? LBM_OK : LBM_EDIVERGED;
+}
+
+lbm_status lbm_batch_set_mass(lbm_batch_t b, int slot, double mass)
+{
+    double now = 0.0;
+    lbm_status s = lbm_batch_mass(b, slot, &now);
+    if (s != LBM_OK) return s;
+    if (!std::isfinite(mass) || !(mass > 0.0)) return bfail(b, LBM_EINVAL, "mass must be finite and positive");
+    const Slot &sl = b->slots[slot];
+    const double delta = (mass - now) / ((double)sl.p.nx * (double)sl.p.ny);
+    BCK(b, b->ops->add_rest(slot_pop(sl, (int)(b->h_dyn[slot].t & 1)), sl.gd, sl.k, delta, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_get_populations(lbm_batch_t b, int slot, double *f, int on_device)
 {
     lbm_status s = benter(b);

@@ -123,6 +123,7 @@ struct lbm_s {
     int variant;          // interior-kernel variant (-1: general kernel only)
     int num_sms;
     CUtensorMap tmap[2];  // TMA descriptors of the two population sets
+    prc::ClusterGeom cgeo;  // cluster-resident engine (variant LBM_VARIANT_CLUSTER)
     cudaGraphExec_t g20;
     bool have_g20;
     std::string err;
@@ -158,15 +159,28 @@ lbm_status enter(lbm_t h)
 
 void *cur_pop(lbm_t h) { return h->pop[h->t & 1]; }
 
+bool is_cluster(lbm_t h) { return h->variant == LBM_VARIANT_CLUSTER; }
+
+// n steps of the cluster-resident engine in one launch (state after step
+// t_before in pop[t_before & 1])
+lbm_status launch_cluster(lbm_t h, cudaStream_t s, long long t_before, long long n)
+{
+    const bool drho = h->p.drho == LBM_DRHO_CURRENT, force = h->p.fx != 0.0 || h->p.fy != 0.0;
+    CK(h, h->ops->cluster_launch(h->pop[0], h->pop[1], h->gd, h->k, h->snap, h->st, t_before, (int)n, h->cgeo.nc,
+                                 h->cgeo.rpc, h->cgeo.smem, drho, force, s));
+    return LBM_OK;
+}
+
 // one step; the state moves from pop[t&1] to pop[(t+1)&1]
 lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
 {
+    if (is_cluster(h)) return launch_cluster(h, s, t_before, 1);
     const bool epi = ((t_before + 1) % RES_INTERVAL) == 0;
     const int c = (int)(t_before & 1);
     const bool drho = h->p.drho == LBM_DRHO_CURRENT, force = h->p.fx != 0.0 || h->p.fy != 0.0;
     if (h->plan.tma)
-        CK(h, h->ops->variants[h->variant].launch(&h->tmap[c], h->pop[c ^ 1], h->plan, h->gd, h->k, h->snap,
-                                                   h->partials, h->st, drho, epi, force, s));
+        CK(h, h->ops->variants[h->variant].launch(&h->tmap[c], h->pop[c], h->pop[c ^ 1], h->plan, h->gd, h->k,
+                                                   h->snap, h->partials, h->st, drho, epi, force, s));
     if (h->plan.n_edge_ctas > 0)
         CK(h, h->ops->step_general(h->pop[c], h->pop[c ^ 1], h->plan, h->gd, h->k, h->snap, h->partials, h->st,
                                    drho, epi, force, s));
@@ -207,6 +221,16 @@ lbm_status ensure_graph(lbm_t h)
 
 lbm_status enqueue_steps(lbm_t h, long long n)
 {
+    if (is_cluster(h)) {
+        while (n > 0) {  // the device steps in one launch per chunk; no graph needed
+            const long long c = n < (1LL << 30) ? n : (1LL << 30);
+            lbm_status s = launch_cluster(h, h->stream, h->t, c);
+            if (s != LBM_OK) return s;
+            h->t += c;
+            n -= c;
+        }
+        return LBM_OK;
+    }
     while (n > 0) {
         if ((h->t % RES_INTERVAL) == 0 && n >= RES_INTERVAL) {
             lbm_status s = ensure_graph(h);
@@ -285,8 +309,50 @@ lbm_status make_tmaps(lbm_t h)
 
 // Select the interior-kernel variant (-1: general kernel everywhere): plan,
 // TMA descriptors, shared-memory opt-in; drops the captured graph.
+// Geometry of the cluster-resident engine for h's grid: the largest cluster
+// (at most 16 CTAs, one slab of >= 2 rows each) whose slabs fit the shared
+// memory of a CTA and which the device can launch.
+lbm_status cluster_select(lbm_t h, prc::ClusterGeom &g)
+{
+    int optin = 0;
+    CK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const int budget = optin - 1024;  // static shared memory of the kernel
+    for (int nc = prc::CL_MAX_CTAS; nc >= 1; nc--) {
+        const int rpc = (h->p.ny + nc - 1) / nc;
+        const int last = h->p.ny - (nc - 1) * rpc;
+        if (rpc < 2 || last < 2) continue;
+        const size_t smem = prc::cluster_smem_bytes(rpc, h->p.nx, h->ops->elem, h->ops->snap_elem);
+        if (smem > (size_t)budget) continue;
+        CK(h, h->ops->cluster_prepare((int)smem));
+        int active = 0;
+        if (h->ops->cluster_max_active(nc, (int)smem, &active) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (active < 1) continue;
+        g.nc = nc;
+        g.rpc = rpc;
+        g.smem = (int)smem;
+        return LBM_OK;
+    }
+    return fail(h, LBM_EINVAL, "grid too large for the cluster-resident engine");
+}
+
 lbm_status apply_variant(lbm_t h, int variant)
 {
+    if (variant == LBM_VARIANT_CLUSTER) {
+        prc::ClusterGeom g;
+        lbm_status cs = cluster_select(h, g);
+        if (cs != LBM_OK) return cs;
+        h->cgeo = g;
+        h->variant = variant;
+        h->plan = make_plan(h->p, h->num_sms, -1);  // unused by the engine; kept consistent
+        if (h->have_g20) {
+            cudaGraphExecDestroy(h->g20);
+            h->have_g20 = false;
+        }
+        return LBM_OK;
+    }
     if (variant < -1 || variant >= h->ops->nvariants) return fail(h, LBM_EINVAL, "no such variant");
     h->variant = variant;
     h->plan = make_plan(h->p, h->num_sms, variant);
@@ -323,7 +389,13 @@ lbm_status init_handle(lbm_t h, const lbm_params &p, void *ws, size_t ws_bytes, 
     h->t = 0;
     h->have_g20 = false;
     CK(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
-    lbm_status vs = apply_variant(h, h->ops->nvariants > 0 ? 0 : -1);
+    // small grids: the cluster-resident engine; otherwise the first interior
+    // variant (or the general kernel when none is compiled)
+    lbm_status vs = apply_variant(h, LBM_VARIANT_CLUSTER);
+    if (vs != LBM_OK) {
+        h->err.clear();
+        vs = apply_variant(h, h->ops->nvariants > 0 ? 0 : -1);
+    }
     if (vs != LBM_OK) return vs;
     CK(h, cudaMallocHost(&h->st_host, sizeof(DevStatus)));
     // rest state f~ = w(r): zero shifted storage everywhere (padding too);
@@ -515,6 +587,32 @@ lbm_status lbm_run(lbm_t h, double tol, long max_steps, long *steps_done)
     long long left = max_steps;
     k_status_arm<<<1, 1, 0, h->stream>>>(h->st, tol);
     CK(h, cudaGetLastError());
+    if (is_cluster(h)) {
+        // one launch per chunk; the engine stops on the device at the step
+        // whose residual meets tol and writes that state back
+        s = read_status(h);
+        if (s != LBM_OK) return s;
+        long long chunk = 2000;
+        while (!h->st_host->stop && left > 0) {
+            const long long n = left < chunk ? left : chunk;
+            s = launch_cluster(h, h->stream, h->t, n);
+            if (s != LBM_OK) return s;
+            s = read_status(h);
+            if (s != LBM_OK) return s;
+            if (h->st_host->stop && h->st_host->res_step > h->t) {
+                left -= h->st_host->res_step - h->t;
+                h->t = h->st_host->res_step;
+            } else {
+                h->t += n;
+                left -= n;
+            }
+            if (chunk < (1LL << 20)) chunk *= 2;
+        }
+        if (steps_done) *steps_done = (long)(h->t - t0);
+        if (h->st_host->diverged) return fail(h, LBM_EDIVERGED, "residual or mass not finite");
+        if (h->st_host->converged) return LBM_OK;
+        return LBM_ENOTCONVERGED;
+    }
     // align to a residual boundary with single launches
     while (left > 0 && (h->t % RES_INTERVAL) != 0) {
         s = launch_one(h, h->stream, h->t);
@@ -606,6 +704,18 @@ lbm_status lbm_mass(lbm_t h, double *mass)
     if (s != LBM_OK) return s;
     *mass = h->st_host->mass_now;
     return std::isfinite(*mass) ? LBM_OK : LBM_EDIVERGED;
+}
+
+lbm_status lbm_set_mass(lbm_t h, double mass)
+{
+    double now = 0.0;
+    lbm_status s = lbm_mass(h, &now);
+    if (s != LBM_OK) return s;
+    if (!std::isfinite(mass) || !(mass > 0.0)) return fail(h, LBM_EINVAL, "mass must be finite and positive");
+    const double delta = (mass - now) / ((double)h->p.nx * (double)h->p.ny);
+    CK(h, h->ops->add_rest(cur_pop(h), h->gd, h->k, delta, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
 }
 
 lbm_status lbm_fields(lbm_t h, double *rho, double *ux, double *uy, int on_device)
@@ -740,9 +850,14 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
     if (steps < 2) return fail(h, LBM_EINVAL, "autotune needs >= 2 steps");
     steps += steps & 1;  // even: the state returns to its buffer
     const int nv = h->ops->nvariants;
-    if (nv == 0) {
+    const int entry_variant = h->variant;
+    prc::ClusterGeom cg;
+    const bool cluster_ok = cluster_select(h, cg) == LBM_OK;
+    h->err.clear();
+    if (ms_per_step) ms_per_step[nv] = -1.0;
+    if (nv == 0 && !cluster_ok) {
         if (best) *best = -1;
-        return LBM_OK;
+        return apply_variant(h, -1);
     }
     CK(h, cudaStreamSynchronize(h->stream));
     // keep the state: copy the current populations, snapshot and status aside
@@ -760,19 +875,28 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    int arg = -1;
+    int arg = entry_variant;
     double bestms = 1e300;
     lbm_status rs = LBM_OK;
-    for (int v = 0; v < nv && rs == LBM_OK; v++) {
-        rs = apply_variant(h, v);
+    // candidates: the interior variants 0 .. nv-1, then the cluster engine
+    for (int v = 0; v < nv + (cluster_ok ? 1 : 0) && rs == LBM_OK; v++) {
+        const int var = v < nv ? v : LBM_VARIANT_CLUSTER;
+        rs = apply_variant(h, var);
         if (rs != LBM_OK) break;
         // plain steps only: a step index of 0 or 1 (same buffer parity as t)
         // never carries the residual epilogue
         const long long t0 = h->t;
-        for (int i = 0; i < 2 && rs == LBM_OK; i++) rs = launch_one(h, h->stream, h->t & 1), h->t++;  // warm
-        cudaEventRecord(e0, h->stream);
-        for (int i = 0; i < steps && rs == LBM_OK; i++) rs = launch_one(h, h->stream, h->t & 1), h->t++;
-        cudaEventRecord(e1, h->stream);
+        if (var == LBM_VARIANT_CLUSTER) {  // the engine runs many steps per launch
+            rs = launch_cluster(h, h->stream, t0 & 1, 2);
+            cudaEventRecord(e0, h->stream);
+            if (rs == LBM_OK) rs = launch_cluster(h, h->stream, t0 & 1, steps);
+            cudaEventRecord(e1, h->stream);
+        } else {
+            for (int i = 0; i < 2 && rs == LBM_OK; i++) rs = launch_one(h, h->stream, h->t & 1), h->t++;  // warm
+            cudaEventRecord(e0, h->stream);
+            for (int i = 0; i < steps && rs == LBM_OK; i++) rs = launch_one(h, h->stream, h->t & 1), h->t++;
+            cudaEventRecord(e1, h->stream);
+        }
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -780,9 +904,9 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
         if (ms_per_step) ms_per_step[v] = per;
         if (per < bestms) {
             bestms = per;
-            arg = v;
+            arg = var;
         }
-        h->t = t0;  // even number of launches: the state is back in pop[t & 1]
+        h->t = t0;  // even number of steps: the state is back in pop[t & 1]
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

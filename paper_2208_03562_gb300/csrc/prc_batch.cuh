@@ -120,10 +120,19 @@ template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
 __device__ __forceinline__ void batch_tile_t(const BatchInst &I, const Coef<T> &k, int parity, int lt,
                                              double2 *partials)
 {
+    __shared__ T srho[srho_floats(BX * BY)];
     const int x0 = (lt % I.tiles_x) * BX, y0 = (lt / I.tiles_x) * BY;
-    general_tile<S, T, DRHO, EPI, FORCE, true>(static_cast<const S *>(I.pop[parity]), static_cast<S *>(I.pop[parity ^ 1]),
-                                         I.gd, k, static_cast<T *>(I.snap), x0, y0, I.gd.nx, I.gd.ny,
-                                         partials + I.part_base + lt);
+    RedAcc<T> acc;
+    general_tile<S, T, DRHO, EPI, FORCE, true>(static_cast<const S *>(I.pop[parity]),
+                                               static_cast<S *>(I.pop[parity ^ 1]), I.gd, k,
+                                               static_cast<T *>(I.snap), x0, y0, I.gd.nx, I.gd.ny, 5, acc, srho);
+    if constexpr (EPI) {
+        __shared__ double red[2 * (BX * BY / 32)];
+        double a, b;
+        acc.block_total(a, b, red);
+        if (threadIdx.x == 0 && threadIdx.y == 0) partials[I.part_base + lt] = make_double2(a, b);
+        __syncthreads();  // red may be reused by the next tile of this CTA
+    }
 }
 
 template <typename S, typename T>

@@ -1,0 +1,250 @@
+// prc_cluster.cuh -- cluster-resident engine for small grids.
+//
+// One thread-block cluster holds a whole instance in distributed shared
+// memory for many time steps.  CTA c of the cluster owns the rows
+// [c rpc, min((c + 1) rpc, ny)) ("slab"), both population sets of its slab
+// and a density tile of the slab plus a one-node ring.  One time step:
+//   1. density tile: rho - rho0 of every slab node and of the ring, each from
+//      its nine pulled populations (App. A streaming; reading A1 for ghost
+//      nodes); pulls of rows outside the slab read the neighbouring CTA's
+//      shared memory through the cluster's distributed shared memory;
+//   2. CTA barrier;
+//   3. every slab node: pull, density gradient from the tile, collision
+//      (the same `collide` as every other kernel, so the populations are
+//      bitwise those of the general kernel), store into the other set;
+//   4. cluster barrier: the new set is complete before anyone pulls from it.
+// Every 20th step of the absolute step counter the CTAs add their FP64
+// residual / mass totals in rank order (identically in every CTA, so the
+// stop decision is uniform and no CTA waits on a barrier the others skip).
+// The state is read from global memory at launch and written back at the end,
+// so a launch of n steps costs one global read and write of the state instead
+// of n; steps are separated by cluster barriers instead of kernel launches.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "prc_kernels.cuh"
+
+namespace prc {
+
+constexpr int CL_THREADS = 512;
+constexpr int CL_MAX_CTAS = 16;
+
+struct ClusterGeom {
+    int nc;    // CTAs (slabs)
+    int rpc;   // rows per slab (the last may be shorter, never below 2)
+    int smem;  // dynamic shared memory per CTA (bytes)
+};
+
+// Shared-memory footprint of a slab of `rows` rows, nx wide.
+__host__ __device__ inline size_t cluster_smem_bytes(int rows, int nx, size_t elem, size_t telem)
+{
+    const size_t f = 2 * 9 * (size_t)rows * nx * elem;
+    const size_t fa = (f + 15) / 16 * 16;
+    return fa + (size_t)(rows + 2) * (nx + 2) * telem;
+}
+
+// Read access to one population set of the cluster: this CTA's slab, the
+// two neighbouring slabs (rows within two of the slab) and, across a periodic
+// wrap, any slab.
+template <typename S, typename T>
+struct SlabView {
+    const S *own, *prev, *next;  // the set in this CTA and in the neighbouring CTAs
+    int y_lo, y_hi, rpc, nx, nc;
+    long long plane;             // rpc * nx (same layout in every CTA)
+
+    __device__ __forceinline__ T ld(int i, int x, int y) const
+    {
+        const S *base;
+        int ly;
+        if (y >= y_lo && y < y_hi) {
+            base = own;
+            ly = y - y_lo;
+        } else if (y < y_lo && y >= y_lo - 2) {
+            base = prev;
+            ly = y - (y_lo - rpc);
+        } else if (y >= y_hi && y < y_hi + 2) {
+            base = next;
+            ly = y - y_hi;
+        } else {  // periodic wrap across the first / last slab
+            auto cl = cooperative_groups::this_cluster();
+            const int owner = min(y / rpc, nc - 1);
+            base = cl.map_shared_rank(const_cast<S *>(own), owner);
+            ly = y - owner * rpc;
+        }
+        return ld_smem<S, T>(base + (long long)i * plane + (long long)ly * nx + x);
+    }
+};
+
+// Pull-streaming with half-way bounce-back and the lid (as pull9) through
+// the slab view.
+template <typename S, typename T>
+__device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &gd, int x, int y, T lid, T g[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        int sx = x - ex_of(i), sy = y - ey_of(i);
+        if (gd.bc >= 1) sx = sx < 0 ? sx + gd.nx : (sx >= gd.nx ? sx - gd.nx : sx);
+        if (gd.bc == 2) sy = sy < 0 ? sy + gd.ny : (sy >= gd.ny ? sy - gd.ny : sy);
+        const bool inside = (sx >= 0) & (sx < gd.nx) & (sy >= 0) & (sy < gd.ny);
+        if (inside) {
+            g[i] = v.ld(i, sx, sy);
+        } else {
+            T w = v.ld(opp_of(i), x, y);
+            if (sy >= gd.ny && gd.lid_on) {
+                if (i == 7) w -= lid;
+                if (i == 8) w += lid;
+            }
+            g[i] = w;
+        }
+    }
+}
+
+// n time steps of one instance on one cluster (gridDim.x == cluster size).
+// pop_in holds the state after step t0; the state after the last step done
+// goes to pop_out[parity of that step].
+template <typename S, typename T, bool DRHO, bool FORCE>
+__global__ void __launch_bounds__(CL_THREADS, 1)
+k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<T> k, T *__restrict__ snap,
+          DevStatus *__restrict__ st, long long t0, int nsteps, int rpc)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    __shared__ double2 part;      // this CTA's residual / mass totals
+    __shared__ double red[2 * (CL_THREADS / 32)];
+    __shared__ int sh_stop;
+
+    if (st->stop) return;  // uniform: read before any write by this launch
+    const int nc = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int nx = gd.nx;
+    SlabView<S, T> v;
+    v.rpc = rpc;
+    v.nx = nx;
+    v.nc = nc;
+    v.y_lo = rank * rpc;
+    v.y_hi = min(v.y_lo + rpc, gd.ny);
+    v.plane = (long long)rpc * nx;
+    const int rows = v.y_hi - v.y_lo;
+    const size_t fbytes = (2 * 9 * (size_t)rpc * nx * sizeof(S) + 15) / 16 * 16;
+    S *F0 = reinterpret_cast<S *>(cl_smem);
+    S *F1 = F0 + 9 * v.plane;
+    T *rho = reinterpret_cast<T *>(cl_smem + fbytes);
+    const int RW = nx + 2;
+    const int prv = rank > 0 ? rank - 1 : nc - 1, nxt = rank + 1 < nc ? rank + 1 : 0;
+    const S *prev0 = cl.map_shared_rank(F0, prv), *prev1 = cl.map_shared_rank(F1, prv);
+    const S *next0 = cl.map_shared_rank(F0, nxt), *next1 = cl.map_shared_rank(F1, nxt);
+
+    // load the slab of the current state
+    const S *pin = (t0 & 1) ? pop1 : pop0;
+    const int nslab = rows * nx;
+    for (int i = 0; i < 9; i++)
+        for (int q = tid; q < nslab; q += nthr) {
+            const int ly = q / nx, x = q - ly * nx;
+            F0[i * v.plane + (long long)ly * nx + x] =
+                pin[(long long)i * gd.plane + (long long)(v.y_lo + ly) * gd.pitch + x];
+        }
+    cl.sync();
+
+    int b = 0;  // set holding the state
+    int done = 0;
+    const double nnodes = (double)gd.nx * (double)gd.ny;
+    for (; done < nsteps; done++) {
+        const long long t = t0 + done + 1;  // absolute index of the step being made
+        const bool epi = (t % 20) == 0;
+        v.own = b ? F1 : F0;
+        v.prev = b ? prev1 : prev0;
+        v.next = b ? next1 : next0;
+        S *Fo = b ? F0 : F1;
+        // 1. density tile (slab + ring)
+        if constexpr (DRHO) {
+            const int nr = (rows + 2) * RW;
+            for (int q = tid; q < nr; q += nthr) {
+                const int ly = q / RW - 1, lx = q - (ly + 1) * RW - 1;
+                int gx = lx, gy = v.y_lo + ly;
+                map_node(gd, gx, gy);
+                T g[9];
+                pull9_slab<S, T>(v, gd, gx, gy, k.lid, g);
+                rho[q] = sum9(g);
+            }
+            __syncthreads();
+        }
+        // 2. collide every slab node into the other set
+        RedAcc<T> acc;
+        for (int q = tid; q < nslab; q += nthr) {
+            const int ly = q / nx, x = q - ly * nx;
+            const int y = v.y_lo + ly;
+            T g[9];
+            pull9_slab<S, T>(v, gd, x, y, k.lid, g);
+            T dxr = T(0), dyr = T(0);
+            if constexpr (DRHO) {
+                const T *c = rho + (ly + 1) * RW + x + 1;
+                const T rE = c[1], rW = c[-1];
+                const T rN = c[RW], rS = c[-RW];
+                const T rNE = c[RW + 1], rNW = c[RW - 1];
+                const T rSE = c[-RW + 1], rSW = c[-RW - 1];
+                dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
+                dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+            }
+            T ux, uy, drho;
+            collide<T, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
+            const long long o = (long long)ly * nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; i++) Fo[i * v.plane + o] = to_s<S, T>(g[i]);
+            if (epi) {
+                const long long og = (long long)y * gd.pitch + x;
+                const T d = ux - snap[og];
+                snap[og] = ux;
+                acc.add(d * d, drho);
+            }
+        }
+        if (epi) {
+            double a, bb;
+            acc.block_total(a, bb, red);
+            if (tid == 0) part = make_double2(a, bb);
+        }
+        // 3. the new set is complete (and every pull of the old one done)
+        cl.sync();
+        b ^= 1;
+        if (epi) {
+            if (tid == 0) {
+                double a = 0.0, m = 0.0;
+                for (int r = 0; r < nc; r++) {  // rank order: the same sums in every CTA
+                    const double2 p = *cl.map_shared_rank(&part, r);
+                    a += p.x;
+                    m += p.y;
+                }
+                const double res = sqrt(a), mass = nnodes + m;
+                int stop = 0;
+                if (!isfinite(res) || !isfinite(mass)) stop = 2;
+                else if (res < st->tol) stop = 1;
+                sh_stop = stop;
+                if (rank == 0) {
+                    st->res_step = t;
+                    st->res = res;
+                    st->mass = mass;
+                    if (stop == 2) st->diverged = 1;
+                    if (stop == 1) st->converged = 1;
+                    if (stop) st->stop = 1;
+                }
+            }
+            cl.sync();  // every CTA has read the partials before they may change
+            if (sh_stop) {
+                done++;
+                break;
+            }
+        }
+    }
+    // write the slab of the final state
+    const long long tend = t0 + done;
+    S *pout = const_cast<S *>((tend & 1) ? pop1 : pop0);
+    for (int i = 0; i < 9; i++)
+        for (int q = tid; q < nslab; q += nthr) {
+            const int ly = q / nx, x = q - ly * nx;
+            pout[(long long)i * gd.plane + (long long)(v.y_lo + ly) * gd.pitch + x] =
+                (b ? F1 : F0)[i * v.plane + (long long)ly * nx + x];
+        }
+}
+
+}  // namespace prc

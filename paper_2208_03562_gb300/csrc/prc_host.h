@@ -31,7 +31,7 @@ inline const prc::DtypeOps *ops_for(int dtype)
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-inline void add_rect(prc::Rects &rc, int x0, int y0, int x1, int y1)
+inline void add_rect(prc::Rects &rc, int x0, int y0, int x1, int y1, int lw, int threads)
 {
     if (x1 <= x0 || y1 <= y0) return;
     const int i = rc.n++;
@@ -39,14 +39,38 @@ inline void add_rect(prc::Rects &rc, int x0, int y0, int x1, int y1)
     rc.y0[i] = y0;
     rc.x1[i] = x1;
     rc.y1[i] = y1;
-    rc.tiles_x[i] = ceil_div(x1 - x0, prc::BX);
-    rc.start[i + 1] = rc.start[i] + rc.tiles_x[i] * ceil_div(y1 - y0, prc::BY);
+    rc.lw[i] = lw;
+    rc.tiles_x[i] = ceil_div(x1 - x0, 1 << lw);
+    rc.start[i + 1] = rc.start[i] + rc.tiles_x[i] * ceil_div(y1 - y0, threads >> lw);
+}
+
+// Tile width (log2) for a w x h strip covered by CTAs of `threads` threads:
+// the fewest tiles, then the widest (coalesced rows).
+inline int strip_lw(int w, int h, int threads)
+{
+    int best = 1;
+    long long best_tiles = -1;
+    for (int lw = 1; (2 << lw) <= threads; lw++) {
+        const long long t = (long long)ceil_div(w, 1 << lw) * ceil_div(h, threads >> lw);
+        if (best_tiles < 0 || t <= best_tiles) {
+            best = lw;
+            best_tiles = t;
+        }
+    }
+    return best;
+}
+
+inline void add_strip(prc::Rects &rc, int x0, int y0, int x1, int y1, int threads)
+{
+    add_rect(rc, x0, y0, x1, y1, strip_lw(x1 - x0, y1 - y0, threads), threads);
 }
 
 // Split of one step between the TMA interior kernel (tiles at least two nodes
-// from every wall, x origin 16-byte aligned) and the general kernel on the
-// remaining edge strips.  num_sms <= 0 gives the upper bound used to size the
-// workspace.
+// from every wall, x origin 16-byte aligned) and the general tile body on the
+// remaining edge strips.  With the interior kernel, the strips are covered by
+// the same launch after its interior tiles (tile shapes fitted to the strips);
+// otherwise the general kernel covers the whole domain in 32 x 8 tiles.
+// num_sms <= 0 gives the upper bound used to size the workspace.
 inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
 {
     const prc::DtypeOps *ops = ops_for(p.dtype);
@@ -57,6 +81,7 @@ inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
     const int PX = ops->tma_padx;
     const int ix0 = PX, iy0 = 2;
     if (have && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
+        const int threads = ops->variants[variant].threads;
         const int xlast = ((p.nx - 2 - W) / PX) * PX;
         const int ylast = p.ny - 2 - H;
         const int xend = xlast + W, yend = ylast + H;
@@ -72,14 +97,15 @@ inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
         const int resident = num_sms * ops->variants[variant].ctas_per_sm;
         if (num_sms > 0 && g > resident) g = resident;
         pl.n_int_ctas = g;
-        add_rect(pl.edge, 0, 0, p.nx, iy0);
-        add_rect(pl.edge, 0, yend, p.nx, p.ny);
-        add_rect(pl.edge, 0, iy0, ix0, yend);
-        add_rect(pl.edge, xend, iy0, p.nx, yend);
+        add_strip(pl.edge, 0, 0, p.nx, iy0, threads);
+        add_strip(pl.edge, 0, yend, p.nx, p.ny, threads);
+        add_strip(pl.edge, 0, iy0, ix0, yend, threads);
+        add_strip(pl.edge, xend, iy0, p.nx, yend, threads);
+        pl.n_edge_ctas = 0;  // the strips ride in the interior launch
     } else {
-        add_rect(pl.edge, 0, 0, p.nx, p.ny);
+        add_rect(pl.edge, 0, 0, p.nx, p.ny, 5, prc::BX * prc::BY);
+        pl.n_edge_ctas = pl.edge.start[pl.edge.n];
     }
-    pl.n_edge_ctas = pl.edge.start[pl.edge.n];
     pl.nparts = pl.n_int_ctas + pl.n_edge_ctas;
     return pl;
 }

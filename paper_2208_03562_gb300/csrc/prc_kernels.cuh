@@ -7,32 +7,56 @@
 
 namespace prc {
 
-constexpr int BX = 32;  // tile width  (nodes, one per thread)
-constexpr int BY = 8;   // tile height
-constexpr int NRING = 2 * (BX + 2) + 2 * BY;
+constexpr int BX = 32;  // default tile width  (nodes, one per thread)
+constexpr int BY = 8;   // default tile height
+constexpr int MAX_RECTS = 4;
 
-// Rectangles of nodes handled by the general kernel (the whole domain, or the
-// edge strips around the interior tiles of the TMA kernel), enumerated as a
-// 1-D list of BX x BY tiles.
+// Rectangles of nodes handled by the general tile body (the whole domain, or
+// the edge strips around the interior tiles of the TMA kernel), enumerated as
+// a 1-D list of tiles.  Each rectangle has its own tile shape: 2^lw nodes wide
+// and (CTA threads) >> lw high, so that thin strips are covered without idle
+// threads.
 struct Rects {
     int n;
-    int x0[4], y0[4], x1[4], y1[4];
-    int tiles_x[4];
-    int start[5];  // first tile index of each rectangle; start[n] = total
+    int x0[MAX_RECTS], y0[MAX_RECTS], x1[MAX_RECTS], y1[MAX_RECTS];
+    int lw[MAX_RECTS];       // log2 of the tile width
+    int tiles_x[MAX_RECTS];
+    int start[MAX_RECTS + 1];  // first tile index of each rectangle; start[n] = total
 };
 
-// One fused time step on one BX x BY tile at (x0, y0) of the nodes x < x1,
-// y < y1: pull-stream + walls, density tile (+1 ring) in shared memory for the
-// density gradient, collision, store.  With EPI the tile also accumulates
-// (u_x - u_x,snapshot)^2 and drho for the residual of Sec. 5.2, refreshes the
-// snapshot and writes its FP64 totals to *part_out.  Called by all BX x BY
-// threads of a CTA.
+// Floats of density tile (+ ring) that general_tile needs for a CTA of
+// `threads` threads and any tile width 2 <= 2^lw <= threads / 2.
+__host__ __device__ constexpr int srho_floats(int threads) { return 4 * (threads / 2 + 2); }
+
+// Origin and shape of tile `e` of the rectangle list.
+__device__ __forceinline__ void rect_tile(const Rects &rc, int e, int &x0, int &y0, int &x1, int &y1, int &lw)
+{
+    int r = 0;
+    while (r + 1 < rc.n && e >= rc.start[r + 1]) r++;
+    const int lt = e - rc.start[r];
+    lw = rc.lw[r];
+    const int th = (int)(blockDim.x * blockDim.y) >> lw;
+    x0 = rc.x0[r] + (lt % rc.tiles_x[r]) * (1 << lw);
+    y0 = rc.y0[r] + (lt / rc.tiles_x[r]) * th;
+    x1 = rc.x1[r];
+    y1 = rc.y1[r];
+}
+
+// One fused time step on one tile of 2^lw x (threads >> lw) nodes at (x0, y0)
+// of the nodes x < x1, y < y1 (all threads of the CTA call it): pull-stream +
+// walls, density tile (+1 ring) in shared memory `srho` (srho_floats(threads)
+// values of type T) for the density gradient, collision, store.  With EPI the
+// thread adds (u_x - u_x,snapshot)^2 and drho of its node to `acc` and
+// refreshes the snapshot (residual of Sec. 5.2).
 template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool CG = false>
 __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__restrict__ dst, const Grid &gd,
                                              const Coef<T> &k, T *__restrict__ snap, int x0, int y0, int x1, int y1,
-                                             double2 *part_out)
+                                             int lw, RedAcc<T> &acc, T *srho)
 {
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int tw = 1 << lw, th = nthr >> lw;
+    const int tx = tid & (tw - 1), ty = tid >> lw;
     const int x = x0 + tx, y = y0 + ty;
     const bool valid = (x < x1) & (y < y1);
     T snap_old = T(0);
@@ -47,27 +71,27 @@ __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__res
 
     T dxr = T(0), dyr = T(0);
     if constexpr (DRHO) {
-        __shared__ T srho[BY + 2][BX + 2];
-        srho[ty + 1][tx + 1] = sum9(g);
-        const int tid = ty * BX + tx;
-        if (tid < NRING) {
+        const int RW = tw + 2;
+        srho[(ty + 1) * RW + tx + 1] = sum9(g);
+        const int nring = 2 * RW + 2 * th;
+        for (int q = tid; q < nring; q += nthr) {
             int lx, ly;
-            if (tid < BX + 2) { lx = tid; ly = 0; }
-            else if (tid < 2 * (BX + 2)) { lx = tid - (BX + 2); ly = BY + 1; }
-            else if (tid < 2 * (BX + 2) + BY) { lx = 0; ly = tid - 2 * (BX + 2) + 1; }
-            else { lx = BX + 1; ly = tid - 2 * (BX + 2) - BY + 1; }
+            if (q < RW) { lx = q; ly = 0; }
+            else if (q < 2 * RW) { lx = q - RW; ly = th + 1; }
+            else if (q < 2 * RW + th) { lx = 0; ly = q - 2 * RW + 1; }
+            else { lx = tw + 1; ly = q - 2 * RW - th + 1; }
             int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
             map_node(gd, gx, gy);
             T gr[9];
             pull9<S, T, CG>(src, gd, gx, gy, k.lid, gr);
-            srho[ly][lx] = sum9(gr);
+            srho[ly * RW + lx] = sum9(gr);
         }
         __syncthreads();
-        const int cx = tx + 1, cy = ty + 1;
-        const T rE = srho[cy][cx + 1], rW = srho[cy][cx - 1];
-        const T rN = srho[cy + 1][cx], rS = srho[cy - 1][cx];
-        const T rNE = srho[cy + 1][cx + 1], rNW = srho[cy + 1][cx - 1];
-        const T rSE = srho[cy - 1][cx + 1], rSW = srho[cy - 1][cx - 1];
+        const T *c = srho + (ty + 1) * RW + tx + 1;
+        const T rE = c[1], rW = c[-1];
+        const T rN = c[RW], rS = c[-RW];
+        const T rNE = c[RW + 1], rNW = c[RW - 1];
+        const T rSE = c[-RW + 1], rSW = c[-RW - 1];
         dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
         dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
         __syncthreads();  // srho may be refilled by the next tile of this CTA
@@ -79,37 +103,33 @@ __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__res
         const long long o = (long long)y * gd.pitch + x;
 #pragma unroll
         for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>(g[i]);
-    }
-    if constexpr (EPI) {
-        __shared__ double red[2 * (BX * BY / 32)];
-        RedAcc<T> acc;
-        if (valid) {
-            const long long o = (long long)y * gd.pitch + x;
+        if constexpr (EPI) {
             const T d = ux - snap_old;
             __stcs(snap + o, ux);
             acc.add(d * d, drho);
         }
-        double a, b;
-        acc.block_total(a, b, red);
-        if (ty == 0 && tx == 0) *part_out = make_double2(a, b);
-        __syncthreads();  // red may be reused by the next tile of this CTA
     }
 }
 
-// One fused time step on the nodes of `rc` (general kernel); the CTA totals
-// of a residual step go to partials[part0 + blockIdx.x].
+// One fused time step on the nodes of `rc` (general kernel, one tile per
+// CTA); the CTA totals of a residual step go to partials[part0 + blockIdx.x].
 template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(BX * BY)
 k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
-       double2 *__restrict__ partials, const DevStatus *__restrict__ st, Rects rc, int part0)
+       double2 *__restrict__ partials, const DevStatus *__restrict__ st, const __grid_constant__ Rects rc, int part0)
 {
     if (st->stop) return;
-    int r = 0;
-    while (r + 1 < rc.n && (int)blockIdx.x >= rc.start[r + 1]) r++;
-    const int lt = blockIdx.x - rc.start[r];
-    const int x0 = rc.x0[r] + (lt % rc.tiles_x[r]) * BX, y0 = rc.y0[r] + (lt / rc.tiles_x[r]) * BY;
-    general_tile<S, T, DRHO, EPI, FORCE>(src, dst, gd, k, snap, x0, y0, rc.x1[r], rc.y1[r],
-                                         partials + part0 + blockIdx.x);
+    __shared__ T srho[srho_floats(BX * BY)];
+    int x0, y0, x1, y1, lw;
+    rect_tile(rc, blockIdx.x, x0, y0, x1, y1, lw);
+    RedAcc<T> acc;
+    general_tile<S, T, DRHO, EPI, FORCE>(src, dst, gd, k, snap, x0, y0, x1, y1, lw, acc, srho);
+    if constexpr (EPI) {
+        __shared__ double red[2 * (BX * BY / 32)];
+        double a, b;
+        acc.block_total(a, b, red);
+        if (threadIdx.x == 0 && threadIdx.y == 0) partials[part0 + blockIdx.x] = make_double2(a, b);
+    }
 }
 
 // f~ = f^eq(rho, u) (Eq. 12, uncorrected), stored shifted; snapshot = u_x.
@@ -195,6 +215,21 @@ __global__ void k_get_pop(const S *__restrict__ src, Grid gd, Coef<double> k, do
     const long long o = (long long)y * gd.pitch + x;
 #pragma unroll
     for (int i = 0; i < 9; i++) f[i * nn + n] = (double)ld_s<S, T>(src + (long long)i * gd.plane + o) + k.w[i];
+}
+
+// Uniform density shift: f_i += w_i(r) delta at every node (the rest
+// populations carry density and no momentum), rounded to the storage.
+template <typename S, typename T>
+__global__ void k_add_rest(S *__restrict__ pop, Grid gd, Coef<double> k, double delta)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= gd.nx || y >= gd.ny) return;
+    const long long o = (long long)y * gd.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        S *p = pop + (long long)i * gd.plane + o;
+        *p = to_s<S, T>((T)((double)ld_s<S, T>(p) + k.w[i] * delta));
+    }
 }
 
 // Per-CTA FP64 partial sums of sum_i g_i (total mass minus the node count).

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "prc_batch.cuh"
+#include "prc_cluster.cuh"
 #include "prc_kernels.cuh"
 #include "prc_tma.cuh"
 
@@ -28,8 +29,9 @@ struct Plan {
     int tma;           // interior kernel in use
     Interior in;
     int n_int_ctas;    // persistent grid of the interior kernel; partials [0, n_int_ctas)
-    Rects edge;        // rectangles of the general kernel
-    int n_edge_ctas;   // partials [n_int_ctas, n_int_ctas + n_edge_ctas)
+    Rects edge;        // rectangles of the general tile body (edge strips ride in the
+                       // interior launch when tma != 0)
+    int n_edge_ctas;   // general-kernel CTAs: partials [n_int_ctas, n_int_ctas + n_edge_ctas)
     int nparts;
 };
 
@@ -42,9 +44,9 @@ struct Variant {
     int threads;      // CTA size
     int ctas_per_sm;  // resident CTAs per SM (shared memory / register budget)
     cudaError_t (*prepare)();
-    cudaError_t (*launch)(const CUtensorMap *tsrc, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &k,
-                          void *snap, double2 *partials, DevStatus *st, bool drho, bool epi, bool force,
-                          cudaStream_t s);
+    cudaError_t (*launch)(const CUtensorMap *tsrc, const void *src, void *dst, const Plan &pl, const Grid &gd,
+                          const Coef<double> &k, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
+                          bool force, cudaStream_t s);
 };
 
 struct DtypeOps {
@@ -70,6 +72,15 @@ struct DtypeOps {
     cudaError_t (*set_pop)(void *dst, const Grid &gd, const Coef<double> &k, const double *f, cudaStream_t s);
     cudaError_t (*get_pop)(const void *src, const Grid &gd, const Coef<double> &k, double *f, cudaStream_t s);
     cudaError_t (*mass_partial)(const void *src, const Grid &gd, double2 *partials, cudaStream_t s);
+    cudaError_t (*add_rest)(void *pop, const Grid &gd, const Coef<double> &k, double delta, cudaStream_t s);
+    // cluster-resident engine: shared-memory / cluster-size opt-in, how many
+    // clusters of nc CTAs with `smem` bytes fit at once (0: not launchable),
+    // and one launch of n steps from the state after step t0
+    cudaError_t (*cluster_prepare)(int smem);
+    cudaError_t (*cluster_max_active)(int nc, int smem, int *n);
+    cudaError_t (*cluster_launch)(const void *pop0, const void *pop1, const Grid &gd, const Coef<double> &k,
+                                  void *snap, DevStatus *st, long long t0, int n, int nc, int rpc, int smem,
+                                  bool drho, bool force, cudaStream_t s);
 };
 
 extern const DtypeOps ops_f64, ops_f32, ops_f16;

@@ -11,37 +11,46 @@ namespace {
 using S = PRC_S;
 using T = PRC_T;
 
+struct TmaArgs {
+    const CUtensorMap *tsrc;
+    const S *a;
+    S *b;
+    Coef<F2> k;
+    Coef<float> kf;
+    float *sn;
+    double2 *partials;
+    DevStatus *st;
+};
+
 template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
-cudaError_t launch_tma_t(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<F2> &k,
-                         float *sn, double2 *partials, DevStatus *st, cudaStream_t s)
+cudaError_t launch_tma_t(const TmaArgs &x, const Plan &pl, const Grid &gd, cudaStream_t s)
 {
     using Cf = TmaCfg<S, W, H, THREADS>;
     k_step_tma<S, W, H, THREADS, MINB, DRHO, EPI, FORCE><<<pl.n_int_ctas, THREADS, Cf::SMEM, s>>>(
-        *tsrc, b, gd, k, sn, partials, st, pl.in);
+        *x.tsrc, x.a, x.b, gd, x.k, x.kf, x.sn, x.partials, x.st, pl.in, pl.edge);
     return cudaGetLastError();
 }
 
 template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI>
-cudaError_t launch_tma_f(const CUtensorMap *tsrc, S *b, const Plan &pl, const Grid &gd, const Coef<F2> &k,
-                         float *sn, double2 *partials, DevStatus *st, bool force, cudaStream_t s)
+cudaError_t launch_tma_f(const TmaArgs &x, const Plan &pl, const Grid &gd, bool force, cudaStream_t s)
 {
-    if (force) return launch_tma_t<W, H, THREADS, MINB, DRHO, EPI, true>(tsrc, b, pl, gd, k, sn, partials, st, s);
-    return launch_tma_t<W, H, THREADS, MINB, DRHO, EPI, false>(tsrc, b, pl, gd, k, sn, partials, st, s);
+    if (force) return launch_tma_t<W, H, THREADS, MINB, DRHO, EPI, true>(x, pl, gd, s);
+    return launch_tma_t<W, H, THREADS, MINB, DRHO, EPI, false>(x, pl, gd, s);
 }
 
 template <int W, int H, int THREADS, int MINB>
-cudaError_t launch_tma(const CUtensorMap *tsrc, void *dst, const Plan &pl, const Grid &gd, const Coef<double> &kd,
-                       void *snap, double2 *partials, DevStatus *st, bool drho, bool epi, bool force, cudaStream_t s)
+cudaError_t launch_tma(const CUtensorMap *tsrc, const void *src, void *dst, const Plan &pl, const Grid &gd,
+                       const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
+                       bool force, cudaStream_t s)
 {
-    const Coef<F2> k = cast_coef<F2>(kd);
-    S *b = static_cast<S *>(dst);
-    float *sn = static_cast<float *>(snap);
+    const TmaArgs x{tsrc, static_cast<const S *>(src), static_cast<S *>(dst), cast_coef<F2>(kd),
+                    cast_coef<float>(kd), static_cast<float *>(snap), partials, st};
     if (drho) {
-        if (epi) return launch_tma_f<W, H, THREADS, MINB, true, true>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
-        return launch_tma_f<W, H, THREADS, MINB, true, false>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
+        if (epi) return launch_tma_f<W, H, THREADS, MINB, true, true>(x, pl, gd, force, s);
+        return launch_tma_f<W, H, THREADS, MINB, true, false>(x, pl, gd, force, s);
     }
-    if (epi) return launch_tma_f<W, H, THREADS, MINB, false, true>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
-    return launch_tma_f<W, H, THREADS, MINB, false, false>(tsrc, b, pl, gd, k, sn, partials, st, force, s);
+    if (epi) return launch_tma_f<W, H, THREADS, MINB, false, true>(x, pl, gd, force, s);
+    return launch_tma_f<W, H, THREADS, MINB, false, false>(x, pl, gd, force, s);
 }
 
 template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
@@ -153,6 +162,79 @@ cudaError_t op_mass_partial(const void *src, const Grid &gd, double2 *partials, 
     return cudaGetLastError();
 }
 
+cudaError_t op_add_rest(void *pop, const Grid &gd, const Coef<double> &k, double delta, cudaStream_t s)
+{
+    k_add_rest<S, T><<<row_grid(gd), 128, 0, s>>>(static_cast<S *>(pop), gd, k, delta);
+    return cudaGetLastError();
+}
+
+template <bool DRHO, bool FORCE>
+cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const Coef<T> &k, T *snap, DevStatus *st,
+                               long long t0, int n, int nc, int rpc, int smem, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc, 1, 1);
+    cfg.blockDim = dim3(CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE>, p0, p1, gd, k, snap, st, t0, n, rpc);
+}
+
+template <bool DRHO, bool FORCE>
+cudaError_t cluster_attr(int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t op_cluster_prepare(int smem)
+{
+    cudaError_t e;
+    if ((e = cluster_attr<false, false>(smem)) != cudaSuccess) return e;
+    if ((e = cluster_attr<false, true>(smem)) != cudaSuccess) return e;
+    if ((e = cluster_attr<true, false>(smem)) != cudaSuccess) return e;
+    return cluster_attr<true, true>(smem);
+}
+
+cudaError_t op_cluster_max_active(int nc, int smem, int *n)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc, 1, 1);
+    cfg.blockDim = dim3(CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(n, (void *)k_cluster<S, T, true, false>, &cfg);
+}
+
+cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd, const Coef<double> &kd, void *snap,
+                              DevStatus *st, long long t0, int n, int nc, int rpc, int smem, bool drho, bool force,
+                              cudaStream_t s)
+{
+    const Coef<T> k = cast_coef<T>(kd);
+    const S *a = static_cast<const S *>(pop0), *b = static_cast<const S *>(pop1);
+    T *sn = static_cast<T *>(snap);
+    if (drho) {
+        if (force) return cluster_cfg_launch<true, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+        return cluster_cfg_launch<true, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    }
+    if (force) return cluster_cfg_launch<false, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    return cluster_cfg_launch<false, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+}
+
 }  // namespace
 
 #define PRC_VARIANT(W, H, THREADS, MINB) \
@@ -160,6 +242,7 @@ cudaError_t op_mass_partial(const void *src, const Grid &gd, double2 *partials, 
 
 const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), 16 / (int)sizeof(S), PRC_NVARIANTS, {PRC_VARIANTS},
                           op_step_general, sizeof(Coef<T>), op_coef_convert, op_batch_occupancy, op_batch_launch,
-                          op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial};
+                          op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial, op_add_rest,
+                          op_cluster_prepare, op_cluster_max_active, op_cluster_launch};
 
 }  // namespace prc

@@ -14,6 +14,7 @@
 #include <cuda.h>
 
 #include "prc_device.cuh"
+#include "prc_kernels.cuh"
 #include "prc_reduce.cuh"
 
 namespace prc {
@@ -131,24 +132,39 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
     }
 }
 
-// Persistent interior kernel: two neighbouring nodes per thread, collision in
-// packed FP32x2 arithmetic.
+// Persistent step kernel: the interior tiles, one pair of neighbouring nodes
+// per thread (THREADS = H W / 2) with the collision in packed FP32x2
+// arithmetic, then the edge strips (`edge`, general tile body with bounce-back
+// and the lid, plain loads), so that one launch is one time step.
+//
+// Per tile: every thread pulls its pair from the staged planes once and keeps
+// the nine values in registers; the density of the pair (and of one ring unit
+// for the first 2 W/2 + 2 (H + 2) threads) goes to the density tile R; after
+// one barrier the thread forms the density gradient from R and collides.
 template <typename S, int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(THREADS, MINB)
-k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid gd, Coef<F2> k,
-           float *__restrict__ snap, double2 *__restrict__ partials, DevStatus *__restrict__ st, Interior in)
+k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, S *__restrict__ dst, Grid gd,
+           Coef<F2> k, Coef<float> kf, float *__restrict__ snap, double2 *__restrict__ partials,
+           DevStatus *__restrict__ st, Interior in, const __grid_constant__ Rects edge)
 {
     using C = TmaCfg<S, W, H, THREADS>;
+    static_assert(THREADS == H * C::PAIRS, "one node pair per thread");
+    static_assert(2 * C::PAIRS + 2 * C::RH <= THREADS, "one ring unit per thread at most");
+    static_assert(C::R_BYTES >= srho_floats(THREADS) * (int)sizeof(float), "density tile too small for the strips");
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // 128-byte aligned base; offsetting the shared array (rather than casting
+    // through an integer) keeps the accesses in the shared address space
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     S *stage0 = reinterpret_cast<S *>(smem);
     S *stage1 = reinterpret_cast<S *>(smem + C::STAGE_BYTES);
     float *R = reinterpret_cast<float *>(smem + 2 * C::STAGE_BYTES);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE_BYTES + C::R_BYTES);
     constexpr int PE = C::PLANE_BYTES / (int)sizeof(S);  // plane stride in elements
+    constexpr int RING = 2 * C::PAIRS + 2 * C::RH;        // ring units: 2 rows of pairs, 2 columns
 
     const int tid = threadIdx.x;
+    const int ly = tid / C::PAIRS, x = 2 * (tid - ly * C::PAIRS);  // this thread's pair in the tile
     const int ntiles = in.ntx * in.nty;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -172,8 +188,6 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
     };
 
     RedAcc<float> acc;
-    constexpr int NQ = (H * C::PAIRS + C::THREADS - 1) / C::THREADS;  // node pairs per thread per tile
-    float2 snv[EPI ? NQ : 1];  // residual snapshot of this thread's pairs, prefetched
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) issue(tile, stage0, &bar[0]);
     bool in_flight_other = false;  // (thread 0) a copy into the other stage is outstanding
@@ -188,16 +202,13 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
         }
         int x0, y0, ox, oy;
         origin(tile, x0, y0, ox, oy);
+        const bool own = (x0 + x >= ox) & (y0 + ly >= oy);  // the pair is owned by this tile
+        const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
+        float2 snv = make_float2(0.f, 0.f);
         if constexpr (EPI) {
             // the snapshot is touched once per residual step: stream it, and
-            // issue the loads now so that they overlap the copies and the collision
-#pragma unroll
-            for (int j = 0; j < NQ; j++) {
-                const int q = tid + j * C::THREADS;
-                const int ly = q / C::PAIRS, x = 2 * (q - ly * C::PAIRS);
-                if (q < H * C::PAIRS && x0 + x >= ox && y0 + ly >= oy)
-                    snv[j] = __ldcs(reinterpret_cast<const float2 *>(snap + (long long)(y0 + ly) * gd.pitch + x0 + x));
-            }
+            // issue the load now so that it overlaps the copies
+            if (own) snv = __ldcs(reinterpret_cast<const float2 *>(snap + o));
         }
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -210,67 +221,66 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, S *__restrict__ dst, Grid g
             return;
         }
 
+        F2 g[9];
+        pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
+        F2 dxr(0.f), dyr(0.f);
         if constexpr (DRHO) {
-            // density (minus rho0) of the tile rows and the ring rows, by pairs
-            for (int q = tid; q < C::RH * C::PAIRS; q += C::THREADS) {
-                const int ry = q / C::PAIRS, x = 2 * (q - ry * C::PAIRS);  // ry = ly + 1
-                F2 g[9];
-                pull_pair<S, PE>(cur + ry * C::BW + x + C::PADX, g);
-                *reinterpret_cast<float2 *>(R + ry * C::RW + x + 2) = sum9(g).v;
-            }
-            // ring columns lx = -1 and lx = W
-            for (int q = tid; q < 2 * C::RH; q += C::THREADS) {
-                const int ry = q >> 1, lx = (q & 1) ? W : -1;
-                const S *b = cur + ry * C::BW + lx + C::PADX;
-                float sum = 0.f;
+            // density (minus rho0) of the pair, and of one ring unit
+            *reinterpret_cast<float2 *>(R + (ly + 1) * C::RW + x + 2) = sum9(g).v;
+            if (tid < RING) {
+                if (tid < 2 * C::PAIRS) {
+                    const int ry = tid < C::PAIRS ? 0 : H + 1;
+                    const int rx = 2 * (tid < C::PAIRS ? tid : tid - C::PAIRS);
+                    F2 gr[9];
+                    pull_pair<S, PE>(cur + ry * C::BW + rx + C::PADX, gr);
+                    *reinterpret_cast<float2 *>(R + ry * C::RW + rx + 2) = sum9(gr).v;
+                } else {
+                    const int c = tid - 2 * C::PAIRS;
+                    const int ry = c >> 1, lx = (c & 1) ? W : -1;
+                    const S *b = cur + ry * C::BW + lx + C::PADX;
+                    float sum = 0.f;
 #pragma unroll
-                for (int i = 0; i < 9; i++) sum += Pair<S>::one(b + i * PE - ex_of(i));
-                R[ry * C::RW + lx + 2] = sum;
+                    for (int i = 0; i < 9; i++) sum += Pair<S>::one(b + i * PE - ex_of(i));
+                    R[ry * C::RW + lx + 2] = sum;
+                }
             }
             __syncthreads();
+            const float *c = R + (ly + 1) * C::RW + x + 2;
+            const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
+                         Rr = *reinterpret_cast<const float2 *>(c + 2);
+            const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
+                         NM = *reinterpret_cast<const float2 *>(c + C::RW),
+                         NR = *reinterpret_cast<const float2 *>(c + C::RW + 2);
+            const float2 SL = *reinterpret_cast<const float2 *>(c - C::RW - 2),
+                         SM = *reinterpret_cast<const float2 *>(c - C::RW),
+                         SR = *reinterpret_cast<const float2 *>(c - C::RW + 2);
+            const float i12 = kf.inv12, i12r = kf.inv12r;
+            // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
+            // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
+            dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
+                     (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
+            dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
+                     (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
         }
-
+        F2 ux, uy, drho;
+        collide<F2, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
 #pragma unroll
-        for (int j = 0; j < NQ; j++) {
-            const int q = tid + j * C::THREADS;
-            if (q >= H * C::PAIRS) break;
-            const int ly = q / C::PAIRS, x = 2 * (q - ly * C::PAIRS);
-            F2 g[9];
-            pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
-            F2 dxr(0.f), dyr(0.f);
-            if constexpr (DRHO) {
-                const float *c = R + (ly + 1) * C::RW + x + 2;
-                const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
-                             Rr = *reinterpret_cast<const float2 *>(c + 2);
-                const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
-                             NM = *reinterpret_cast<const float2 *>(c + C::RW),
-                             NR = *reinterpret_cast<const float2 *>(c + C::RW + 2);
-                const float2 SL = *reinterpret_cast<const float2 *>(c - C::RW - 2),
-                             SM = *reinterpret_cast<const float2 *>(c - C::RW),
-                             SR = *reinterpret_cast<const float2 *>(c - C::RW + 2);
-                const float i12 = k.inv12.v.x, i12r = k.inv12r.v.x;
-                // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
-                // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
-                dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
-                         (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
-                dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
-                         (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
-            }
-            F2 ux, uy, drho;
-            collide<F2, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
-            const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
-#pragma unroll
-            for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[i]);
-            if constexpr (EPI) {
-                if (x0 + x >= ox && y0 + ly >= oy) {  // the pair is owned by this tile
-                    __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
-                    const float da = ux.v.x - snv[j].x, db = ux.v.y - snv[j].y;
-                    acc.add(da * da, drho.v.x);
-                    acc.add(db * db, drho.v.y);
-                }
+        for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[i]);
+        if constexpr (EPI) {
+            if (own) {
+                __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
+                const float da = ux.v.x - snv.x, db = ux.v.y - snv.y;
+                acc.add(da * da, drho.v.x);
+                acc.add(db * db, drho.v.y);
             }
         }
         __syncthreads();  // stage `cur` and R are free for reuse
+    }
+    // edge strips: general tile body, density tile in R (free now)
+    for (int e = blockIdx.x; e < edge.start[edge.n]; e += gridDim.x) {
+        int ex0, ey0, ex1, ey1, lw;
+        rect_tile(edge, e, ex0, ey0, ex1, ey1, lw);
+        general_tile<S, float, DRHO, EPI, FORCE>(src, dst, gd, kf, snap, ex0, ey0, ex1, ey1, lw, acc, R);
     }
     if constexpr (EPI) {
         __shared__ double red[2 * (THREADS / 32)];

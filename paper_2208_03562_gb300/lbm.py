@@ -19,6 +19,7 @@ BC_CAVITY, BC_CHANNEL, BC_PERIODIC = 0, 1, 2
 DRHO_CURRENT, DRHO_OFF = 0, 1
 
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTCONVERGED = range(7)
+VARIANT_GENERAL, VARIANT_CLUSTER = -1, -2
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDIVERGED", "ETIMEOUT", "ENOTCONVERGED"]
 
 
@@ -68,6 +69,7 @@ def load():
         "lbm_run": [_H, C.c_double, C.c_long, C.POINTER(C.c_long)],
         "lbm_residual": [_H, _D],
         "lbm_mass": [_H, _D],
+        "lbm_set_mass": [_H, C.c_double],
         "lbm_info": [_H, C.POINTER(lbm_info_t)],
         "lbm_sync": [_H],
         "lbm_fields": [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
@@ -99,6 +101,8 @@ def load():
         "lbm_batch_fields": [B, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
         "lbm_batch_set_populations": [B, C.c_int, C.c_void_p, C.c_int],
         "lbm_batch_get_populations": [B, C.c_int, C.c_void_p, C.c_int],
+        "lbm_batch_mass": [B, C.c_int, _D],
+        "lbm_batch_set_mass": [B, C.c_int, C.c_double],
     })
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -128,7 +132,8 @@ def exported_symbols():
                  "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc", "lbm_batch_create",
                  "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_instance_bytes", "lbm_batch_add",
                  "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
-                 "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations"):
+                 "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations",
+                 "lbm_batch_mass", "lbm_batch_set_mass", "lbm_set_mass"):
         if hasattr(L, name):
             out.append(name)
     return out
@@ -217,6 +222,10 @@ def lbm_mass(h) -> float:
     return v.value
 
 
+def lbm_set_mass(h, mass: float):
+    _check(load().lbm_set_mass(h, float(mass)), h)
+
+
 def lbm_info(h) -> lbm_info_t:
     info = lbm_info_t()
     _check(load().lbm_info(h, C.byref(info)), h)
@@ -284,13 +293,14 @@ def lbm_set_variant(h, variant):
 
 
 def lbm_autotune(h, dtype, steps=20):
-    """Time every variant on the handle's grid; selects the fastest.
-    Returns (best, [ms per step of each variant])."""
+    """Time every candidate on the handle's grid; selects the fastest.
+    Returns (best, [ms per step of each interior variant, then of the
+    cluster engine (-1 when it does not fit)])."""
     n = lbm_variant_count(dtype)
-    ms = (C.c_double * max(n, 1))()
+    ms = (C.c_double * (n + 1))()
     best = C.c_int()
     _check(load().lbm_autotune(h, int(steps), C.byref(best), ms), h)
-    return best.value, [ms[i] for i in range(n)]
+    return best.value, [ms[i] for i in range(n + 1)]
 
 
 def lbm_step_noalloc(p: lbm_params, src_ptr: int, dst_ptr: int, snap_ptr: int, with_residual: bool,
@@ -374,6 +384,9 @@ class Lbm:
 
     def info(self):
         return lbm_info(self.h)
+
+    def set_mass(self, mass: float):
+        lbm_set_mass(self.h, mass)
 
     def sync(self):
         lbm_sync(self.h)
@@ -497,6 +510,15 @@ class Batch:
         f = np.empty((9, ny, nx))
         _bcheck(load().lbm_batch_get_populations(self.b, slot, _host_ptr(f), 0), self.b)
         return f
+
+    def mass(self, slot: int) -> float:
+        m = C.c_double()
+        _bcheck(load().lbm_batch_mass(self.b, slot, C.byref(m)), self.b)
+        return m.value
+
+    def set_mass(self, slot: int, mass: float):
+        """Uniform density shift of a slot to the given total mass (see lbm_set_mass)."""
+        _bcheck(load().lbm_batch_set_mass(self.b, slot, float(mass)), self.b)
 
     def populations_to_device(self, slot: int, f_ptr: int):
         """Full FP64 populations of a slot into a device buffer of 9 ny nx doubles."""

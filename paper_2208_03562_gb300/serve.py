@@ -62,6 +62,11 @@ class SolveRequest:
     params: object          # lbm_params; the dtype field is set per stage
     tol: float
     max_steps: int
+    mass0: float = None     # total mass of the initial state (default: rest, nx ny rho0)
+
+    def __post_init__(self):
+        if self.mass0 is None:
+            self.mass0 = float(self.nodes)
 
     @property
     def nodes(self) -> int:
@@ -198,6 +203,10 @@ class SolveServer:
         left = lv.req.max_steps - sum(lv.steps_done)
         slot = self._add(lv.req, nxt, max(1, left))
         self.batches[nxt].set_populations_from_device(slot, ptr)
+        # narrow storage rounds every population and so lets the total mass
+        # drift; a closed cavity conserves it exactly, and its steady state
+        # depends on it: restore the request's initial mass
+        self.batches[nxt].set_mass(slot, lv.req.mass0)
         self.used += nb
         lv.stage, lv.slot, lv.bytes, lv.waiting_promotion = nxt, slot, nb, False
         self.live[(nxt, slot)] = lv
@@ -331,3 +340,48 @@ def summary(server: SolveServer, results: Sequence[SolveResult]) -> dict:
         "wall_s": server.wall_s, "launches": server.launches,
         "steps_p50": percentile([r.steps for r in conv], 50),
     }
+
+
+class _TorchStaging:
+    """Device FP64 promotion buffer from PyTorch's allocator, grown on demand."""
+
+    def __init__(self):
+        self.buf = None
+
+    def __call__(self, n: int) -> int:
+        import torch
+        if self.buf is None or self.buf.numel() < n:
+            self.buf = None
+            self.buf = torch.empty(int(n), dtype=torch.float64, device="cuda")
+        return self.buf.data_ptr()
+
+
+def gpu_server(stages: Sequence[Stage], capacity: int = 256, budget_bytes: Optional[int] = None,
+               reserve_bytes: int = 2 << 30, **kw) -> SolveServer:
+    """A server on the current CUDA device: one lbm.Batch per stage, all on one
+    PyTorch stream, memory budget = free device memory minus reserve_bytes
+    unless budget_bytes is given."""
+    import torch
+
+    from . import lbm as L
+    L.load()
+    stream = torch.cuda.Stream()
+    if budget_bytes is None:
+        free, _ = torch.cuda.mem_get_info()
+        budget_bytes = max(0, free - reserve_bytes)
+
+    def make_batch(cap, dtype):
+        return L.Batch(cap, dtype, stream.cuda_stream)
+
+    def instance_bytes(p, dtype):
+        p.dtype = dtype
+        return L.lbm_batch_instance_bytes(p)
+
+    srv = SolveServer(stages, capacity, budget_bytes, make_batch, instance_bytes, _TorchStaging(), **kw)
+    srv.stream = stream
+    return srv
+
+
+def fp16_schedule(stall_window: int = 2000, stall_ratio: float = 0.9) -> List[Stage]:
+    """FP16 shifted storage until the residual stalls, then FP32 to the tolerance."""
+    return [Stage(2, stall_window, stall_ratio), Stage(1)]

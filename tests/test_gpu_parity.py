@@ -200,7 +200,8 @@ def test_autotune_restores_state_exactly():
     before = g.populations()
     info = g.info()
     best, ms = g.autotune(10)
-    assert 0 <= best < len(ms) and all(m > 0 for m in ms)
+    # interior variants, then the cluster engine (-1: this grid does not fit it)
+    assert 0 <= best < len(ms) - 1 and all(m > 0 for m in ms[:-1]) and ms[-1] == -1.0
     assert g.variant == best
     assert np.array_equal(before, g.populations())
     assert g.info().step == info.step and g.info().residual == info.residual
@@ -295,3 +296,23 @@ def test_full_size_shallow_cavity_fp32_sampled():
     a, b = g.fields(), o.fields()
     assert rel_l2_u(a, b) < 1e-5
     assert abs(g.mass() - oracle_mass(o)) < 1e-6 * cav.nodes
+
+
+@pytest.mark.parametrize("dtype,tol", [(L.F64, 1e-13), (L.F32, 1e-9), (L.F16, 1e-5)])
+def test_set_mass_shifts_density_only(dtype, tol):
+    """lbm_set_mass: the total mass becomes the target, the momentum field
+    sum f e does not change (beyond the storage rounding)."""
+    nx, ny = 40, 24
+    g = L.Lbm(L.lbm_params_init(nx, ny, 0.5, 0.3, 0.01, 0.03, dtype))
+    g.step(200)
+    rho0, ux0, uy0 = g.fields()
+    target = nx * ny * (1.0 + 3e-4)
+    g.set_mass(target)
+    assert abs(g.mass() - target) <= tol * target
+    rho1, ux1, uy1 = g.fields()
+    mom = lambda rho, u: rho * u
+    scale = np.max(np.abs(mom(rho0, ux0))) + 1e-30
+    lim = {L.F64: 1e-14, L.F32: 1e-6, L.F16: 2e-3}[dtype]
+    assert np.max(np.abs(mom(rho1, ux1) - mom(rho0, ux0))) <= lim * scale
+    assert np.max(np.abs(mom(rho1, uy1) - mom(rho0, uy0))) <= lim * scale
+    assert np.allclose(rho1 - rho0, 3e-4, atol=1e-4 if dtype == L.F16 else 1e-9)

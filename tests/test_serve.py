@@ -44,6 +44,7 @@ class FakeWorld:
         self.glups = glups
         self.staged = {}
         self.batches = []
+        self.mass_calls = []
 
     def clock(self):
         return self.t
@@ -134,6 +135,9 @@ class FakeBatch:
         sl = self.slots[slot]
         sl.off, sl.t, sl.state, sl.res = self.w.staged[ptr], 0, SV.SLOT_ACTIVE, math.inf
 
+    def set_mass(self, slot, mass):
+        self.w.mass_calls.append((self.dtype, mass))
+
     def close(self):
         pass
 
@@ -205,6 +209,8 @@ def test_fp16_stall_promotes_to_fp32():
         assert r.status == "converged" and len(r.steps_by_stage) == 2 and r.residual < 1e-6
         # the FP32 stage resumed where FP16 stopped: total progress is continuous
         assert r.fields[0][0, 0] == r.steps
+    # each promoted slot was reset to its request's initial mass (rest: nx ny)
+    assert sorted(w.mass_calls) == [(F32, 64.0 * 32), (F32, 96.0 * 48)]
     assert srv.used == srv.staging_bytes
 
 
@@ -242,3 +248,71 @@ def test_percentile_nearest_rank():
     xs = list(range(1, 101))
     assert SV.percentile(xs, 50) == 50 and SV.percentile(xs, 99) == 99 and SV.percentile(xs, 100) == 100
     assert math.isnan(SV.percentile([], 50))
+
+
+# ---------------------------------------------------------------------------
+# GPU: the real engine
+
+def _gpu_or_skip():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2208_03562_gb300 import lbm as L
+    L.load()
+    return L
+
+
+def _cavity_request(L, rid, arrival, nx, ny, r, gamma, re, u, tol=1e-6, max_steps=400000):
+    nu = u * ny * r / re
+    return SV.SolveRequest(rid, arrival, L.lbm_params_init(nx, ny, r, gamma, nu, u, L.F16), tol, max_steps)
+
+
+@pytest.mark.gpu
+def test_gpu_server_alone_equals_mix():
+    """One solve alone and among requests that arrive while it runs: the same
+    steps in each stage, the same residual and bitwise the same fields."""
+    L = _gpu_or_skip()
+    x = lambda: _cavity_request(L, 0, 0.0, 96, 48, 0.5, 0.3, 100.0, 0.03)
+    srv = SV.gpu_server(SV.fp16_schedule(1000), capacity=16, chunk_node_steps=2e7)
+    alone = srv.serve([x()])[0]
+    srv.close()
+    others = [_cavity_request(L, 1, 0.0, 64, 64, 1.0, 0.5, 100.0, 0.05),
+              _cavity_request(L, 2, 0.01, 130, 40, 0.25, 0.2, 300.0, 0.02),
+              _cavity_request(L, 3, 0.02, 70, 90, 2.0, 1.0, 100.0, 0.04),
+              _cavity_request(L, 4, 0.05, 200, 30, 0.5, 0.1, 500.0, 0.02),
+              _cavity_request(L, 5, 0.1, 33, 17, 1.0, 0.7, 50.0, 0.05)]
+    srv = SV.gpu_server(SV.fp16_schedule(1000), capacity=16, chunk_node_steps=2e7)
+    mix = {r.rid: r for r in srv.serve([x()] + others)}
+    srv.close()
+    assert srv.launches > 2
+    m = mix[0]
+    assert alone.status == "converged" and m.status == "converged"
+    assert m.steps_by_stage == alone.steps_by_stage and m.residual == alone.residual
+    for a, b in zip(alone.fields, m.fields):
+        assert np.array_equal(a, b)
+    assert len(mix) == 6
+
+
+@pytest.mark.gpu
+def test_gpu_server_schedule_matches_oracle():
+    """FP16 until the residual stalls, then FP32. Run to residual 1e-7 (FP32
+    storage itself stalls near 7e-8 on this grid), the schedule lands on the
+    FP64 oracle's steady field within 5e-5 (relative L2 of u; the distance
+    left at that residual is ~2e-5): the FP16 transient leaves no trace.
+    Stopped at 1e-6, the field is still ~2e-4 from steady (as any run stopped
+    there), within the 1e-3 bound of the FP16 storage path at steady state."""
+    L = _gpu_or_skip()
+    from oracle import stepper as S
+    nx, ny, r, gamma, U, re = 64, 32, 0.5, 0.25, 0.05, 100.0
+    o = S.Oracle(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=U * ny * r / re, u_lid=U))
+    o.run(1e-11, 600000)
+    _, oux, ouy = o.fields()
+    for tol, bound in ((1e-7, 5e-5), (1e-6, 1e-3)):
+        req = _cavity_request(L, 0, 0.0, nx, ny, r, gamma, re, U, tol=tol, max_steps=600000)
+        srv = SV.gpu_server(SV.fp16_schedule(1000), capacity=4)
+        res = srv.serve([req])[0]
+        srv.close()
+        assert res.status == "converged" and len(res.steps_by_stage) == 2, res
+        _, ux, uy = res.fields
+        e = math.sqrt(np.sum((ux - oux) ** 2 + (uy - ouy) ** 2) / np.sum(oux ** 2 + ouy ** 2))
+        assert e < bound, (tol, e)

@@ -1,0 +1,62 @@
+"""Step-count / stability / grid-saving studies (paper_2208_03562_gb300.sweep).
+
+CPU tests check the experiment table against the paper's printed grids and
+the definitions of Ma, Re and the lid speed. The GPU test checks the two
+claims of Sec. 5.2 that need no external data: preconditioning (gamma < 1)
+cuts the steps to a residual by a large factor, and it leaves the steady
+field unchanged.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2208_03562_gb300 import sweep as SW
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_experiments_match_the_printed_grids():
+    with open(os.path.join(GOLDEN, "paper_grids.json")) as fh:
+        cases = json.load(fh)["cases"]
+    printed = {(c["nx"], c["ny"], c["r"]) for c in cases}
+    for e in SW.PAPER_EXPERIMENTS:
+        assert (e.nx, e.ny, round(e.r, 2)) in printed, e.name
+        # Sec. 5.2: r = AR Nx / Ny
+        assert abs(e.ar * e.nx / e.ny - e.r) < 1e-2
+
+
+def test_lid_speed_and_viscosity_from_mach_and_reynolds():
+    e = SW.PAPER_EXPERIMENTS[0]  # shallow, r = 0.2, Ma = 0.06, Re = 100
+    assert math.isclose(e.u_lid, 0.06 * 0.2 / math.sqrt(3.0), rel_tol=1e-15)  # Ma = U / (q c_s*), q = r < 1
+    assert math.isclose(e.u_lid * e.ny * e.r / e.nu, e.re, rel_tol=1e-12)      # Re = U H / nu, H = ny r
+    d = SW.PAPER_EXPERIMENTS[2]  # deep, r = 1.6 > 1: q = 1
+    assert math.isclose(d.u_lid, 0.06 / math.sqrt(3.0), rel_tol=1e-15)
+
+
+def test_centreline_profiles_pick_the_middle():
+    ny, nx = 6, 5
+    ux = np.tile(np.arange(nx, dtype=float), (ny, 1))
+    uy = np.tile(np.arange(ny, dtype=float)[:, None], (1, nx))
+    ys, u_c, xs, v_c = SW.centreline_profiles((None, ux, uy), nx, ny, 1.0)
+    assert np.all(u_c == 2.0)               # odd nx: the middle column
+    assert np.all(v_c == 2.5)               # even ny: mean of the two middle rows
+    assert np.allclose(ys, (np.arange(ny) + 0.5) / ny)
+
+
+@pytest.mark.gpu
+def test_preconditioning_cuts_steps_and_keeps_the_steady_field():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    e = SW.Experiment("shallow_Ma0.06", "Sec. 5.2", 0.25, 0.2, 100, 125, 100.0, 0.06, (1.0, 0.1))
+    res = SW.convergence_study(e, tol=1e-6, want_fields=True, max_steps=4_000_000)
+    g1, g01 = res["runs"]
+    assert g1["status"] == g01["status"] == "converged"
+    assert g01["step_reduction_vs_gamma1"] > 5.0, res
+    _, u1, v1 = g1["fields"]
+    _, u2, v2 = g01["fields"]
+    rel = math.sqrt(np.sum((u1 - u2) ** 2 + (v1 - v2) ** 2) / np.sum(u1 ** 2 + v1 ** 2))
+    assert rel < 2e-3, rel
