@@ -68,6 +68,14 @@ typedef enum {
     LBM_DRHO_OFF = 1      /* density-gradient terms dropped                     */
 } lbm_drho;
 
+typedef enum {
+    LBM_MODEL_PRC = 0,  /* central moments: PRC-LBM (Sec. 4.2, App. A), default    */
+    LBM_MODEL_PRNR = 1  /* raw moments: PRNR-LBM (Sec. 4.1, Eq.
+                           LBErawmomentrectangularlattice; compared in Sec. 5.3);
+                           same corrections, higher-order rates 1; runs on the
+                           general kernel and the cluster engine               */
+} lbm_model;
+
 /*
  * Run parameters.  nu is the kinematic shear viscosity; the shear relaxation
  * rate follows Eq. transport-coefficients, nu = gamma q^2 c_s*^2
@@ -84,7 +92,7 @@ typedef struct {
     int32_t dtype; /* lbm_dtype */
     int32_t bc;    /* lbm_bc    */
     int32_t drho;  /* lbm_drho  */
-    int32_t reserved;
+    int32_t model; /* lbm_model */
 } lbm_params;
 
 /* Progress record filled by lbm_info. */
@@ -98,13 +106,13 @@ typedef struct {
 } lbm_info_t;
 
 /* Fill p with the defaults: cavity walls, omega_xi = 1, no force,
- * LBM_DRHO_CURRENT, and the given values. EINVAL if p is NULL. */
+ * LBM_DRHO_CURRENT, LBM_MODEL_PRC, and the given values. EINVAL if p is NULL. */
 lbm_status lbm_params_init(lbm_params *p, int nx, int ny, double r, double gamma,
                            double nu, double u_lid, int dtype);
 
 /* Check p without allocating: nx, ny >= 3; r > 0; 0 < gamma <= 1; nu > 0 with
  * 0 < omega_nu < 2; 0 < omega_xi < 2; |u_lid| < q c_s*; dtype, bc, drho in
- * range; nx * ny * 9 populations addressable. */
+ * range; model in range; nx * ny * 9 populations addressable. */
 lbm_status lbm_params_check(const lbm_params *p);
 
 /* Device bytes a handle needs for p (two population sets, u_x snapshot,

@@ -183,3 +183,75 @@ def collide(f, r, gamma, omega_nu, dxrho=0.0, dyrho=0.0, fx=0.0, fy=0.0,
     nct = nc + Lam @ (nceq - nc) + (np.eye(9) - Lam / 2) @ psi
     ft = np.linalg.inv(P) @ np.linalg.inv(S) @ np.linalg.inv(B) @ F_matrix(-ux, -uy) @ nct
     return ft, np.array([rho, ux, uy, dxux, dyuy])
+
+
+def collide_raw(f, r, gamma, omega_nu, dxrho=0.0, dyrho=0.0, fx=0.0, fy=0.0,
+                omega_3=1.0, omega_6=1.0, omega_7=1.0, omega_8=1.0, corrections=True):
+    """PRNR-LBM collision of one node, as the matrix product of
+    Eq. 10-equivalent:
+
+        f~ = P^-1 S^-1 [ m + B^-1 Lambda (B m^eq - B m) + B^-1 (I - Lambda/2) B Phi ]
+
+    with m = S P f, the raw equilibria of Eq. 12 (second order extended by the
+    corrections of Eqs. 30-31 with the coefficients of Eqs. 38-40), the raw
+    sources of Eq. 13 and Lambda of Eq. 11. The strain rates of the corrections
+    come from Eq. 45, as in the central scheme. Returns (f~, diag)."""
+    f = np.asarray(f, dtype=np.float64)
+    q = min(1.0, r)
+    c2 = q * q * CS_STAR2
+    g = gamma
+    P, S, B = P_matrix(), S_matrix(r), B_matrix()
+    m = S @ P @ f
+    n = B @ m
+    rho = n[0]
+    ux = (n[1] + fx / (2 * g)) / rho
+    uy = (n[2] + fy / (2 * g)) / rho
+    # the correction terms (second order only) are the central scheme's: the
+    # difference of the two equilibria in the combined basis at order two
+    _, diag = collide(f, r, gamma, omega_nu, dxrho, dyrho, fx, fy, omega_3, omega_6, omega_7, omega_8,
+                      corrections)
+    corr = _corrections(rho, ux, uy, diag[3], diag[4], dxrho, dyrho, r, g, c2, omega_3, omega_nu) \
+        if corrections else np.zeros(9)
+    meq = np.array([
+        rho, rho * ux, rho * uy,
+        2 * c2 * rho + rho * (ux ** 2 + uy ** 2) / g,
+        rho * (ux ** 2 - uy ** 2) / g,
+        rho * ux * uy / g,
+        rho * (c2 + ux ** 2 / g ** 2) * uy,
+        rho * (c2 + uy ** 2 / g ** 2) * ux,
+        rho * c2 ** 2 + rho * c2 * (ux ** 2 + uy ** 2) + rho * ux ** 2 * uy ** 2,
+    ]) + corr
+    s20, s02 = 2 * fx * ux / g ** 2, 2 * fy * uy / g ** 2
+    phi = np.array([0.0, fx / g, fy / g, s20 + s02, s20 - s02, (fx * uy + fy * ux) / g ** 2, 0.0, 0.0, 0.0])
+    Lam = np.diag([0.0, 0.0, 0.0, omega_3, omega_nu, omega_nu, omega_6, omega_7, omega_8])
+    Bi = np.linalg.inv(B)
+    mt = m + Bi @ Lam @ (meq - n) + Bi @ (np.eye(9) - Lam / 2) @ phi
+    ft = np.linalg.inv(P) @ np.linalg.inv(S) @ mt
+    return ft, diag
+
+
+def _corrections(rho, ux, uy, dxux, dyuy, dxrho, dyrho, r, g, c2, w3, w4):
+    """Eq. 31 with the coefficients of Eqs. 38-40 (combined basis, second order)."""
+    w5 = w4
+    M3 = rho * ((4 / g ** 2 - 1 / g) * ux ** 2 + (1 / g ** 2 - 1 / g) * uy ** 2)
+    N3 = rho * ((4 / g ** 2 - 1 / g) * uy ** 2 + (1 / g ** 2 - 1 / g) * ux ** 2)
+    M4 = rho * ((4 / g ** 2 - 1 / g) * ux ** 2 - (1 / g ** 2 - 1 / g) * uy ** 2)
+    N4 = rho * (-(4 / g ** 2 - 1 / g) * uy ** 2 + (1 / g ** 2 - 1 / g) * ux ** 2)
+    t3, t4, t5 = 1 / w3 - 0.5, 1 / w4 - 0.5, 1 / w5 - 0.5
+    th3x = -(M3 + (3 * c2 - 1) * rho) * t3
+    th3y = -(N3 + (3 * c2 - r ** 2) * rho) * t3
+    la3x = -((2 / g + 1) * c2 - 1) * t3 * ux
+    la3y = -((2 / g + 1) * c2 - r ** 2) * t3 * uy
+    th4x = -(M4 + (3 * c2 - 1) * rho) * t4
+    th4y = +(N4 - (3 * c2 - r ** 2) * rho) * t4
+    la4x = -((2 / g + 1) * c2 - 1) * t4 * ux
+    la4y = +((2 / g + 1) * c2 - r ** 2) * t4 * uy
+    th5x = -(1 / g ** 2 - 1 / g) * t5 * rho * ux * uy
+    th5y = -(1 / g ** 2 - 1 / g) * t5 * rho * ux * uy
+    la5x = -(1 / g - 1) * t5 * c2 * uy
+    la5y = -(1 / g - 1) * t5 * c2 * ux
+    corr = np.zeros(9)
+    corr[3] = th3x * dxux + th3y * dyuy + la3x * dxrho + la3y * dyrho
+    corr[4] = th4x * dxux - th4y * dyuy + la4x * dxrho + la4y * dyrho
+    corr[5] = th5x * dxux + th5y * dyuy + la5x * dxrho + la5y * dyrho
+    return corr

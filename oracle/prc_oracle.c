@@ -48,6 +48,13 @@
  *       (App. A); they are parameters here so that the matrix form of
  *       Eq. 10-equivalent-centralmoment can be cross-checked with any rates.
  *   A8  Residual ||u_x(t) - u_x(t-20)||_2 (Sec. 5.2), unnormalised, FP64.
+ *   A12 PRNR-LBM (model = 1, Sec. 4.1 and Sec. 5.3): the raw-moment scheme of
+ *       Eq. LBErawmomentrectangularlattice, m = S P f, relaxation of B m to
+ *       the raw equilibria of Eq. 12 with the raw sources of Eq. 13, then
+ *       B^-1, S^-1, P^-1.  The paper applies "the corrections ... given in
+ *       Sec. 3.4" to its second-order equilibria; they are the same
+ *       expressions as in the central scheme, with the strain rates of
+ *       Eq. 45, which is written for the central non-equilibrium moments.
  *
  * State layout: the post-collision populations f~ of the last completed
  * step, f~[i][y][x], i = 0..8, y = 0..ny-1, x = 0..nx-1 (x fastest).  One
@@ -77,6 +84,8 @@ typedef struct {
     int bc;
     int drho_off;    /* 1: density-gradient terms set to zero            */
     int corrections; /* 1: extended equilibria (Eq. 30-40); 0: Eq. 14    */
+    int model;       /* 0: PRC-LBM (central moments, Sec. 4.2, App. A);
+                        1: PRNR-LBM (raw moments, Sec. 4.1 and Sec. 5.3)   */
 } orc_params;
 
 /* Per-run constants derived once from the parameters. */
@@ -269,50 +278,82 @@ static void collide(const orc_consts *c, const double f[9], double dxrho, double
         eq11_corr = ttheta_sx * dxux + ttheta_sy * dyuy + tlambda_sx * dxrho + tlambda_sy * dyrho;
     }
 
-    /* -- preconditioned central-moment equilibria (Eq. 14 + corrections), dt = 1 -- */
-    double eq10 = 0.0, eq01 = 0.0;
-    double eq2s = 2 * cs2 * rho + (1.0 / g - 1.0) * rho * (ux2 + uy2) + eq2s_corr;
-    double eq2d = (1.0 / g - 1.0) * rho * (ux2 - uy2) + eq2d_corr;
-    double eq11 = (1.0 / g - 1.0) * rho * ux * uy + eq11_corr;
-    double eq21 = (1.0 / (g * g) - 3.0 / g + 2.0) * rho * ux2 * uy;
-    double eq12 = (1.0 / (g * g) - 3.0 / g + 2.0) * rho * ux * uy2;
-    double eq22 = cs2 * cs2 * rho;
+    double m00, m10, m01, m20, m02, m11, m21, m12, m22;
+    if (p->model == 0) {
+        /* -- preconditioned central-moment equilibria (Eq. 14 + corrections), dt = 1 -- */
+        double eq10 = 0.0, eq01 = 0.0;
+        double eq2s = 2 * cs2 * rho + (1.0 / g - 1.0) * rho * (ux2 + uy2) + eq2s_corr;
+        double eq2d = (1.0 / g - 1.0) * rho * (ux2 - uy2) + eq2d_corr;
+        double eq11 = (1.0 / g - 1.0) * rho * ux * uy + eq11_corr;
+        double eq21 = (1.0 / (g * g) - 3.0 / g + 2.0) * rho * ux2 * uy;
+        double eq12 = (1.0 / (g * g) - 3.0 / g + 2.0) * rho * ux * uy2;
+        double eq22 = cs2 * cs2 * rho;
 
-    /* -- central moments of the source (Eq. 13-central) -- */
-    const double fx = p->fx, fy = p->fy;
-    double s10 = fx / g, s01 = fy / g;
-    double s20 = (1.0 / (g * g) - 1.0 / g) * 2 * fx * ux;
-    double s02 = (1.0 / (g * g) - 1.0 / g) * 2 * fy * uy;
-    double s11 = (1.0 / (g * g) - 1.0 / g) * (fx * uy + fy * ux);
-    double s2s = s20 + s02, s2d = s20 - s02;
+        /* -- central moments of the source (Eq. 13-central) -- */
+        const double fx = p->fx, fy = p->fy;
+        double s10 = fx / g, s01 = fy / g;
+        double s20 = (1.0 / (g * g) - 1.0 / g) * 2 * fx * ux;
+        double s02 = (1.0 / (g * g) - 1.0 / g) * 2 * fy * uy;
+        double s11 = (1.0 / (g * g) - 1.0 / g) * (fx * uy + fy * ux);
+        double s2s = s20 + s02, s2d = s20 - s02;
 
-    /* -- relaxation (App. A), dt = 1 -- */
-    const double w1 = p->omega_1;
-    double t00 = c00;
-    double t10 = c10 + w1 * (eq10 - c10) + (1 - w1 / 2) * s10;
-    double t01 = c01 + w1 * (eq01 - c01) + (1 - w1 / 2) * s01;
-    double t2s = c2s + wxi * (eq2s - c2s) + (1 - wxi / 2) * s2s;
-    double t2d = c2d + wnu * (eq2d - c2d) + (1 - wnu / 2) * s2d;
-    double t11 = c11 + wnu * (eq11 - c11) + (1 - wnu / 2) * s11;
-    double t21 = c21 + p->omega_21 * (eq21 - c21);
-    double t12 = c12 + p->omega_12 * (eq12 - c12);
-    double t22 = c22 + p->omega_22 * (eq22 - c22);
+        /* -- relaxation (App. A), dt = 1 -- */
+        const double w1 = p->omega_1;
+        double t00 = c00;
+        double t10 = c10 + w1 * (eq10 - c10) + (1 - w1 / 2) * s10;
+        double t01 = c01 + w1 * (eq01 - c01) + (1 - w1 / 2) * s01;
+        double t2s = c2s + wxi * (eq2s - c2s) + (1 - wxi / 2) * s2s;
+        double t2d = c2d + wnu * (eq2d - c2d) + (1 - wnu / 2) * s2d;
+        double t11 = c11 + wnu * (eq11 - c11) + (1 - wnu / 2) * s11;
+        double t21 = c21 + p->omega_21 * (eq21 - c21);
+        double t12 = c12 + p->omega_12 * (eq12 - c12);
+        double t22 = c22 + p->omega_22 * (eq22 - c22);
 
-    /* -- segregate (operator B^-1, reading A2) -- */
-    double t20 = 0.5 * (t2s + t2d);
-    double t02 = 0.5 * (t2s - t2d);
+        /* -- segregate (operator B^-1, reading A2) -- */
+        double t20 = 0.5 * (t2s + t2d);
+        double t02 = 0.5 * (t2s - t2d);
 
-    /* -- post-collision raw moments m~ = F^-1 m~^c (reading A5) -- */
-    double m00 = t00;
-    double m10 = t10 + ux * t00;
-    double m01 = t01 + uy * t00;
-    double m20 = t20 + 2 * ux * t10 + ux2 * t00;
-    double m02 = t02 + 2 * uy * t01 + uy2 * t00;
-    double m11 = t11 + uy * t10 + ux * t01 + ux * uy * t00;
-    double m21 = t21 + 2 * ux * t11 + ux2 * t01 + uy * t20 + 2 * ux * uy * t10 + ux2 * uy * t00;
-    double m12 = t12 + 2 * uy * t11 + uy2 * t10 + ux * t02 + 2 * ux * uy * t01 + ux * uy2 * t00;
-    double m22 = t22 + 2 * ux * t12 + ux2 * t02 + 2 * uy * t21 + 4 * ux * uy * t11
-               + 2 * ux2 * uy * t01 + uy2 * t20 + 2 * ux * uy2 * t10 + ux2 * uy2 * t00;
+        /* -- post-collision raw moments m~ = F^-1 m~^c (reading A5) -- */
+        m00 = t00;
+        m10 = t10 + ux * t00;
+        m01 = t01 + uy * t00;
+        m20 = t20 + 2 * ux * t10 + ux2 * t00;
+        m02 = t02 + 2 * uy * t01 + uy2 * t00;
+        m11 = t11 + uy * t10 + ux * t01 + ux * uy * t00;
+        m21 = t21 + 2 * ux * t11 + ux2 * t01 + uy * t20 + 2 * ux * uy * t10 + ux2 * uy * t00;
+        m12 = t12 + 2 * uy * t11 + uy2 * t10 + ux * t02 + 2 * ux * uy * t01 + ux * uy2 * t00;
+        m22 = t22 + 2 * ux * t12 + ux2 * t02 + 2 * uy * t21 + 4 * ux * uy * t11
+                   + 2 * ux2 * uy * t01 + uy2 * t20 + 2 * ux * uy2 * t10 + ux2 * uy2 * t00;
+    } else {
+        /* PRNR-LBM (Eq. LBErawmomentrectangularlattice): relax the combined
+           raw moments B m towards the raw equilibria of Eq. 12, whose second
+           order carries the same corrections (Sec. 3.4; reading A12: the
+           strain rates are those of Eq. 45 as above), with the raw sources of
+           Eq. 13 and the rates of Eq. 11 (zero for the conserved moments). */
+        const double r2s = k20 + k02, r2d = k20 - k02;
+        const double eq2s = 2 * cs2 * rho + rho * (ux2 + uy2) / g + eq2s_corr;
+        const double eq2d = rho * (ux2 - uy2) / g + eq2d_corr;
+        const double eq11 = rho * ux * uy / g + eq11_corr;
+        const double eq21 = rho * (cs2 + ux2 / (g * g)) * uy;
+        const double eq12 = rho * (cs2 + uy2 / (g * g)) * ux;
+        const double eq22 = rho * cs2 * cs2 + rho * cs2 * (ux2 + uy2) + rho * ux2 * uy2;
+        const double fx = p->fx, fy = p->fy;
+        const double s10 = fx / g, s01 = fy / g;
+        const double s20 = 2 * fx * ux / (g * g), s02 = 2 * fy * uy / (g * g);
+        const double s11 = (fx * uy + fy * ux) / (g * g);
+        const double t2s = r2s + wxi * (eq2s - r2s) + (1 - wxi / 2) * (s20 + s02);
+        const double t2d = r2d + wnu * (eq2d - r2d) + (1 - wnu / 2) * (s20 - s02);
+        m00 = k00;
+        m10 = k10 + s10;
+        m01 = k01 + s01;
+        m11 = k11 + wnu * (eq11 - k11) + (1 - wnu / 2) * s11;
+        m21 = k21 + p->omega_21 * (eq21 - k21);
+        m12 = k12 + p->omega_12 * (eq12 - k12);
+        m22 = k22 + p->omega_22 * (eq22 - k22);
+        /* segregate (B^-1, reading A2) */
+        m20 = 0.5 * (t2s + t2d);
+        m02 = 0.5 * (t2s - t2d);
+    }
 
     /* -- inverse scaling: factor r^-n for k~'_mn -- */
     m01 /= r;

@@ -22,7 +22,7 @@ class _Params(C.Structure):
         ("omega_xi", C.c_double), ("omega_1", C.c_double), ("omega_21", C.c_double),
         ("omega_12", C.c_double), ("omega_22", C.c_double),
         ("fx", C.c_double), ("fy", C.c_double),
-        ("bc", C.c_int), ("drho_off", C.c_int), ("corrections", C.c_int),
+        ("bc", C.c_int), ("drho_off", C.c_int), ("corrections", C.c_int), ("model", C.c_int),
     ]
 
 
@@ -45,6 +45,7 @@ class OracleParams:
     bc: int = BC_CAVITY
     drho_off: int = 0
     corrections: int = 1
+    model: int = 0  # 0: PRC-LBM (central moments); 1: PRNR-LBM (raw moments)
 
     def c(self) -> _Params:
         d = asdict(self)

@@ -354,6 +354,8 @@ lbm_status apply_variant(lbm_t h, int variant)
         return LBM_OK;
     }
     if (variant < -1 || variant >= h->ops->nvariants) return fail(h, LBM_EINVAL, "no such variant");
+    if (variant >= 0 && h->p.model != LBM_MODEL_PRC)
+        return fail(h, LBM_EINVAL, "the interior kernel implements the central scheme only");
     h->variant = variant;
     h->plan = make_plan(h->p, h->num_sms, variant);
     if (h->plan.tma) {
@@ -394,7 +396,7 @@ lbm_status init_handle(lbm_t h, const lbm_params &p, void *ws, size_t ws_bytes, 
     lbm_status vs = apply_variant(h, LBM_VARIANT_CLUSTER);
     if (vs != LBM_OK) {
         h->err.clear();
-        vs = apply_variant(h, h->ops->nvariants > 0 ? 0 : -1);
+        vs = apply_variant(h, h->ops->nvariants > 0 && p.model == LBM_MODEL_PRC ? 0 : -1);
     }
     if (vs != LBM_OK) return vs;
     CK(h, cudaMallocHost(&h->st_host, sizeof(DevStatus)));
@@ -427,6 +429,7 @@ lbm_status lbm_params_init(lbm_params *p, int nx, int ny, double r, double gamma
     p->dtype = dtype;
     p->bc = LBM_BC_CAVITY;
     p->drho = LBM_DRHO_CURRENT;
+    p->model = LBM_MODEL_PRC;
     return LBM_OK;
 }
 
@@ -448,6 +451,7 @@ lbm_status lbm_params_check(const lbm_params *p)
     if (!ops_for(p->dtype)) return fail(nullptr, LBM_EINVAL, "unknown dtype");
     if (p->bc < LBM_BC_CAVITY || p->bc > LBM_BC_PERIODIC) return fail(nullptr, LBM_EINVAL, "unknown bc");
     if (p->drho != LBM_DRHO_CURRENT && p->drho != LBM_DRHO_OFF) return fail(nullptr, LBM_EINVAL, "unknown drho");
+    if (p->model != LBM_MODEL_PRC && p->model != LBM_MODEL_PRNR) return fail(nullptr, LBM_EINVAL, "unknown model");
     return LBM_OK;
 }
 
@@ -849,7 +853,7 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
     if (s != LBM_OK) return s;
     if (steps < 2) return fail(h, LBM_EINVAL, "autotune needs >= 2 steps");
     steps += steps & 1;  // even: the state returns to its buffer
-    const int nv = h->ops->nvariants;
+    const int nv = h->p.model == LBM_MODEL_PRC ? h->ops->nvariants : 0;
     const int entry_variant = h->variant;
     prc::ClusterGeom cg;
     const bool cluster_ok = cluster_select(h, cg) == LBM_OK;

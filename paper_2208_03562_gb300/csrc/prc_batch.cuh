@@ -116,14 +116,14 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl)
     return ok != 0;
 }
 
-template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool RAW>
 __device__ __forceinline__ void batch_tile_t(const BatchInst &I, const Coef<T> &k, int parity, int lt,
                                              double2 *partials)
 {
     __shared__ T srho[srho_floats(BX * BY)];
     const int x0 = (lt % I.tiles_x) * BX, y0 = (lt / I.tiles_x) * BY;
     RedAcc<T> acc;
-    general_tile<S, T, DRHO, EPI, FORCE, true>(static_cast<const S *>(I.pop[parity]),
+    general_tile<S, T, DRHO, EPI, FORCE, true, RAW>(static_cast<const S *>(I.pop[parity]),
                                                static_cast<S *>(I.pop[parity ^ 1]), I.gd, k,
                                                static_cast<T *>(I.snap), x0, y0, I.gd.nx, I.gd.ny, 5, acc, srho);
     if constexpr (EPI) {
@@ -135,27 +135,35 @@ __device__ __forceinline__ void batch_tile_t(const BatchInst &I, const Coef<T> &
     }
 }
 
+template <typename S, typename T, bool RAW>
+__device__ __forceinline__ void batch_tile_m(const BatchInst &I, const Coef<T> &k, int parity, int lt, bool epi,
+                                             double2 *partials)
+{
+    if (I.drho) {
+        if (I.force) {
+            if (epi) batch_tile_t<S, T, true, true, true, RAW>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, true, false, true, RAW>(I, k, parity, lt, partials);
+        } else {
+            if (epi) batch_tile_t<S, T, true, true, false, RAW>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, true, false, false, RAW>(I, k, parity, lt, partials);
+        }
+    } else {
+        if (I.force) {
+            if (epi) batch_tile_t<S, T, false, true, true, RAW>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, false, false, true, RAW>(I, k, parity, lt, partials);
+        } else {
+            if (epi) batch_tile_t<S, T, false, true, false, RAW>(I, k, parity, lt, partials);
+            else batch_tile_t<S, T, false, false, false, RAW>(I, k, parity, lt, partials);
+        }
+    }
+}
+
 template <typename S, typename T>
 __device__ __forceinline__ void batch_tile(const BatchInst &I, const Coef<T> &k, int parity, int lt, bool epi,
                                            double2 *partials)
 {
-    if (I.drho) {
-        if (I.force) {
-            if (epi) batch_tile_t<S, T, true, true, true>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, true, false, true>(I, k, parity, lt, partials);
-        } else {
-            if (epi) batch_tile_t<S, T, true, true, false>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, true, false, false>(I, k, parity, lt, partials);
-        }
-    } else {
-        if (I.force) {
-            if (epi) batch_tile_t<S, T, false, true, true>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, false, false, true>(I, k, parity, lt, partials);
-        } else {
-            if (epi) batch_tile_t<S, T, false, true, false>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, false, false, false>(I, k, parity, lt, partials);
-        }
-    }
+    if (I.gd.model == 1) batch_tile_m<S, T, true>(I, k, parity, lt, epi, partials);
+    else batch_tile_m<S, T, false>(I, k, parity, lt, epi, partials);
 }
 
 template <typename S, typename T>

@@ -53,6 +53,17 @@ struct SlabView {
     int y_lo, y_hi, rpc, nx, nc;
     long long plane;             // rpc * nx (same layout in every CTA)
 
+    // plane-0 address of the in-domain row y (any slab)
+    __device__ __forceinline__ const S *row(int y) const
+    {
+        if (y >= y_lo && y < y_hi) return own + (long long)(y - y_lo) * nx;
+        if (y < y_lo && y >= y_lo - 2) return prev + (long long)(y - (y_lo - rpc)) * nx;
+        if (y >= y_hi && y < y_hi + 2) return next + (long long)(y - y_hi) * nx;
+        auto cl = cooperative_groups::this_cluster();
+        const int owner = min(y / rpc, nc - 1);
+        return cl.map_shared_rank(const_cast<S *>(own), owner) + (long long)(y - owner * rpc) * nx;
+    }
+
     __device__ __forceinline__ T ld(int i, int x, int y) const
     {
         const S *base;
@@ -77,10 +88,23 @@ struct SlabView {
 };
 
 // Pull-streaming with half-way bounce-back and the lid (as pull9) through
-// the slab view.
+// the slab view.  Nodes whose nine sources are all inside the domain (away
+// from the x walls, and away from the y walls unless y is periodic) take the
+// fast path: the three source rows are resolved once and the nine pulls are
+// fixed offsets from them.
 template <typename S, typename T>
 __device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &gd, int x, int y, T lid, T g[9])
 {
+    const bool xin = (x >= 1) & (x <= gd.nx - 2);
+    const bool yin = (gd.bc == 2) | ((y >= 1) & (y <= gd.ny - 2));
+    if (xin & yin) {
+        const int ym = y == 0 ? gd.ny - 1 : y - 1, yp = y == gd.ny - 1 ? 0 : y + 1;
+        const S *rr[3] = {v.row(ym), v.row(y), v.row(yp)};  // source row of e_y = +1, 0, -1
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            g[i] = ld_smem<S, T>(rr[1 - ey_of(i)] + (long long)i * v.plane + (x - ex_of(i)));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
@@ -103,7 +127,7 @@ __device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &
 // n time steps of one instance on one cluster (gridDim.x == cluster size).
 // pop_in holds the state after step t0; the state after the last step done
 // goes to pop_out[parity of that step].
-template <typename S, typename T, bool DRHO, bool FORCE>
+template <typename S, typename T, bool DRHO, bool FORCE, bool RAW>
 __global__ void __launch_bounds__(CL_THREADS, 1)
 k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<T> k, T *__restrict__ snap,
           DevStatus *__restrict__ st, long long t0, int nsteps, int rpc)
@@ -131,7 +155,6 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     S *F0 = reinterpret_cast<S *>(cl_smem);
     S *F1 = F0 + 9 * v.plane;
     T *rho = reinterpret_cast<T *>(cl_smem + fbytes);
-    const int RW = nx + 2;
     const int prv = rank > 0 ? rank - 1 : nc - 1, nxt = rank + 1 < nc ? rank + 1 : 0;
     const S *prev0 = cl.map_shared_rank(F0, prv), *prev1 = cl.map_shared_rank(F1, prv);
     const S *next0 = cl.map_shared_rank(F0, nxt), *next1 = cl.map_shared_rank(F1, nxt);
@@ -139,6 +162,13 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     // load the slab of the current state
     const S *pin = (t0 & 1) ? pop1 : pop0;
     const int nslab = rows * nx;
+    // this thread's nodes q = tid + k nthr of the slab (ly = q / nx, x = q % nx)
+    // and of the density tile (q / RW, q % RW), advanced without divisions
+    const int RW = nx + 2;
+    const int s_dly = nthr / nx, s_dx = nthr - s_dly * nx;
+    const int s_ly0 = tid / nx, s_x0 = tid - s_ly0 * nx;
+    const int r_dly = nthr / RW, r_dx = nthr - r_dly * RW;
+    const int r_ly0 = tid / RW, r_x0 = tid - r_ly0 * RW;
     for (int i = 0; i < 9; i++)
         for (int q = tid; q < nslab; q += nthr) {
             const int ly = q / nx, x = q - ly * nx;
@@ -160,8 +190,15 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
         // 1. density tile (slab + ring)
         if constexpr (DRHO) {
             const int nr = (rows + 2) * RW;
+            int ry = r_ly0, rx = r_x0;
             for (int q = tid; q < nr; q += nthr) {
-                const int ly = q / RW - 1, lx = q - (ly + 1) * RW - 1;
+                const int ly = ry - 1, lx = rx - 1;
+                rx += r_dx;
+                ry += r_dly;
+                if (rx >= RW) {
+                    rx -= RW;
+                    ry++;
+                }
                 int gx = lx, gy = v.y_lo + ly;
                 map_node(gd, gx, gy);
                 T g[9];
@@ -172,8 +209,15 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
         }
         // 2. collide every slab node into the other set
         RedAcc<T> acc;
+        int sy_ = s_ly0, sx_ = s_x0;
         for (int q = tid; q < nslab; q += nthr) {
-            const int ly = q / nx, x = q - ly * nx;
+            const int ly = sy_, x = sx_;
+            sx_ += s_dx;
+            sy_ += s_dly;
+            if (sx_ >= nx) {
+                sx_ -= nx;
+                sy_++;
+            }
             const int y = v.y_lo + ly;
             T g[9];
             pull9_slab<S, T>(v, gd, x, y, k.lid, g);
@@ -188,7 +232,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
             }
             T ux, uy, drho;
-            collide<T, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
+            collide<T, DRHO, FORCE, RAW>(k, g, dxr, dyr, ux, uy, drho);
             const long long o = (long long)ly * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; i++) Fo[i * v.plane + o] = to_s<S, T>(g[i]);

@@ -50,6 +50,7 @@ struct Coef {
     T fsx, fsy, fdx, fdy;      // (1 - omega/2) Q_gamma F: source moments (Eq. 13-central)
     T nig, nr2, nhPg, nhQg, nk3y, ninv_r2, nfdy;  // negated copies
     T lid;                     // c^2 U / (2 r^2): moving-lid bounce-back term
+    T ig2;                     // 1 / g^2 (raw-moment scheme)
     T inv12, inv12r;           // 1/12, 1/(12 r): density-gradient stencil
     T w[9];                    // rest populations w_i(r)
 };
@@ -60,7 +61,7 @@ struct Grid {
     int bc;           // 0 cavity, 1 channel (x-periodic), 2 periodic
     long long plane;  // elements per plane
     int lid_on;       // top wall moves
-    int pad;
+    int model;        // 0: central moments (PRC-LBM); 1: raw moments (PRNR-LBM)
 };
 
 // Device-side run status (one per instance).
@@ -153,7 +154,13 @@ PRC_HD T sum9(const T g[9])
 // the file header), generic over float, double and packed F2.
 // In: g[9] streamed shifted populations, density gradient (dxr, dyr).
 // Out: g[9] post-collision shifted populations; u_x, u_y, drho of the node.
-template <typename T, bool DRHO, bool FORCE>
+// RAW selects the raw-moment scheme (PRNR-LBM, Eq.
+// LBErawmomentrectangularlattice, Sec. 5.3) instead of the central one: its
+// post-collision raw moments of orders 0-2 are the same (the non-equilibrium
+// second-order moments and the sources agree between the frames), and those
+// of orders 3-4 are the raw equilibria of Eq. 12 (rates 1) instead of the
+// binomial transform of the central ones.
+template <typename T, bool DRHO, bool FORCE, bool RAW = false>
 PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out, T &drho_out)
 {
     // square-lattice raw moments of the deviations (Eq. 62 applied to g)
@@ -238,10 +245,19 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
     T D20 = vadd(vadd(c2s00, rux2), dt20);
     T D02 = vadd(vadd(c2s00, ruy2), dt02);
     T D11 = vadd(t11, ruxy);
-    T D21 = vfma(k.a3p1, e21, vfma(vadd(ux, ux), t11, vmul(uy, t20)));
-    T D12 = vfma(k.a3p1, e12, vfma(vadd(uy, uy), t11, vmul(ux, t02)));
-    T D22 = vfma(ux2, t02, vfma(uy2, t20, vfma(vmul(splat<T>(4.0), uxy), t11,
-                                                vfma(k.a34p1, vmul(e21, uy), vmul(k.c4, s00)))));
+    T D21, D12, D22;
+    if constexpr (RAW) {
+        // raw equilibria of Eq. 12: rho (c^2 + u_x^2 / g^2) u_y, rho (c^2 +
+        // u_y^2 / g^2) u_x, rho c^4 + rho c^2 (u_x^2 + u_y^2) + rho u_x^2 u_y^2
+        D21 = vfma(k.c2, jy, vmul(k.ig2, e21));
+        D12 = vfma(k.c2, jx, vmul(k.ig2, e12));
+        D22 = vfma(k.c4, s00, vfma(k.c2, sp, vmul(e21, uy)));
+    } else {
+        D21 = vfma(k.a3p1, e21, vfma(vadd(ux, ux), t11, vmul(uy, t20)));
+        D12 = vfma(k.a3p1, e12, vfma(vadd(uy, uy), t11, vmul(ux, t02)));
+        D22 = vfma(ux2, t02, vfma(uy2, t20, vfma(vmul(splat<T>(4.0), uxy), t11,
+                                                 vfma(k.a34p1, vmul(e21, uy), vmul(k.c4, s00)))));
+    }
     if (FORCE) {
         const T hxuy = vmul(k.hx, uy), hyux = vmul(k.hy, ux);
         D10 = vadd(D10, k.hx);
@@ -249,9 +265,11 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
         D20 = vfma(vadd(ux, ux), k.hx, D20);
         D02 = vfma(vadd(uy, uy), k.hy, D02);
         D11 = vadd(D11, vadd(hxuy, hyux));
-        D21 = vfma(ux, vfma(splat<T>(2.0), hxuy, hyux), D21);
-        D12 = vfma(uy, vfma(splat<T>(2.0), hyux, hxuy), D12);
-        D22 = vfma(vadd(uxy, uxy), vadd(hxuy, hyux), D22);
+        if constexpr (!RAW) {
+            D21 = vfma(ux, vfma(splat<T>(2.0), hxuy, hyux), D21);
+            D12 = vfma(uy, vfma(splat<T>(2.0), hyux, hxuy), D12);
+            D22 = vfma(vadd(uxy, uxy), vadd(hxuy, hyux), D22);
+        }
     }
 
     // S^-1 then P^-1 (Eq. 72) with the 1/2, 1/4 and 1/r^n factors folded

@@ -80,7 +80,8 @@ inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
     const int W = have ? ops->variants[variant].w : 0, H = have ? ops->variants[variant].h : 0;
     const int PX = ops->tma_padx;
     const int ix0 = PX, iy0 = 2;
-    if (have && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
+    // the interior kernel implements the central scheme only
+    if (have && p.model == LBM_MODEL_PRC && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
         const int threads = ops->variants[variant].threads;
         const int xlast = ((p.nx - 2 - W) / PX) * PX;
         const int ylast = p.ny - 2 - H;
@@ -204,6 +205,7 @@ inline void make_coef(const lbm_params &p, Coef<double> &k)
     k.nfdy = -k.fdy;
     const bool lid_on = (p.bc != LBM_BC_PERIODIC) && (p.u_lid != 0.0);
     k.lid = lid_on ? c2 * p.u_lid / (2.0 * r * r) : 0.0;
+    k.ig2 = 1.0 / (g * g);
     k.inv12 = 1.0 / 12.0;
     k.inv12r = 1.0 / (12.0 * r);
     // rest populations: the unique f with the rest moments (1, 0, 0, c^2,
@@ -224,7 +226,7 @@ inline Grid make_grid(const lbm_params &p, const Layout &L)
     gd.bc = p.bc;
     gd.plane = (long long)L.plane;
     gd.lid_on = (p.bc != LBM_BC_PERIODIC) && (p.u_lid != 0.0);
-    gd.pad = 0;
+    gd.model = p.model;
     return gd;
 }
 

@@ -48,7 +48,7 @@ __device__ __forceinline__ void rect_tile(const Rects &rc, int e, int &x0, int &
 // values of type T) for the density gradient, collision, store.  With EPI the
 // thread adds (u_x - u_x,snapshot)^2 and drho of its node to `acc` and
 // refreshes the snapshot (residual of Sec. 5.2).
-template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool CG = false>
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool CG = false, bool RAW = false>
 __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__restrict__ dst, const Grid &gd,
                                              const Coef<T> &k, T *__restrict__ snap, int x0, int y0, int x1, int y1,
                                              int lw, RedAcc<T> &acc, T *srho)
@@ -99,7 +99,7 @@ __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__res
 
     T ux = T(0), uy = T(0), drho = T(0);
     if (valid) {
-        collide<T, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
+        collide<T, DRHO, FORCE, RAW>(k, g, dxr, dyr, ux, uy, drho);
         const long long o = (long long)y * gd.pitch + x;
 #pragma unroll
         for (int i = 0; i < 9; i++) dst[(long long)i * gd.plane + o] = to_s<S, T>(g[i]);
@@ -113,7 +113,7 @@ __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__res
 
 // One fused time step on the nodes of `rc` (general kernel, one tile per
 // CTA); the CTA totals of a residual step go to partials[part0 + blockIdx.x].
-template <typename S, typename T, bool DRHO, bool EPI, bool FORCE>
+template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool RAW>
 __global__ void __launch_bounds__(BX * BY)
 k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__restrict__ snap,
        double2 *__restrict__ partials, const DevStatus *__restrict__ st, const __grid_constant__ Rects rc, int part0)
@@ -123,7 +123,7 @@ k_step(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<T> k, T *__
     int x0, y0, x1, y1, lw;
     rect_tile(rc, blockIdx.x, x0, y0, x1, y1, lw);
     RedAcc<T> acc;
-    general_tile<S, T, DRHO, EPI, FORCE>(src, dst, gd, k, snap, x0, y0, x1, y1, lw, acc, srho);
+    general_tile<S, T, DRHO, EPI, FORCE, false, RAW>(src, dst, gd, k, snap, x0, y0, x1, y1, lw, acc, srho);
     if constexpr (EPI) {
         __shared__ double red[2 * (BX * BY / 32)];
         double a, b;

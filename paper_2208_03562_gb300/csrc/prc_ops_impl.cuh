@@ -80,8 +80,12 @@ template <bool DRHO, bool EPI, bool FORCE>
 cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn,
                            double2 *partials, const DevStatus *st, cudaStream_t s)
 {
-    k_step<S, T, DRHO, EPI, FORCE><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st, pl.edge,
-                                                                           pl.n_int_ctas);
+    if (gd.model == 1)
+        k_step<S, T, DRHO, EPI, FORCE, true><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st,
+                                                                                     pl.edge, pl.n_int_ctas);
+    else
+        k_step<S, T, DRHO, EPI, FORCE, false><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st,
+                                                                                      pl.edge, pl.n_int_ctas);
     return cudaGetLastError();
 }
 
@@ -168,7 +172,7 @@ cudaError_t op_add_rest(void *pop, const Grid &gd, const Coef<double> &k, double
     return cudaGetLastError();
 }
 
-template <bool DRHO, bool FORCE>
+template <bool DRHO, bool FORCE, bool RAW>
 cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const Coef<T> &k, T *snap, DevStatus *st,
                                long long t0, int n, int nc, int rpc, int smem, cudaStream_t s)
 {
@@ -184,24 +188,32 @@ cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const C
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE>, p0, p1, gd, k, snap, st, t0, n, rpc);
+    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE, RAW>, p0, p1, gd, k, snap, st, t0, n, rpc);
 }
 
-template <bool DRHO, bool FORCE>
+template <bool DRHO, bool FORCE, bool RAW>
 cudaError_t cluster_attr(int smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE, RAW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE, RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <bool RAW>
+cudaError_t cluster_prepare_m(int smem)
+{
+    cudaError_t e;
+    if ((e = cluster_attr<false, false, RAW>(smem)) != cudaSuccess) return e;
+    if ((e = cluster_attr<false, true, RAW>(smem)) != cudaSuccess) return e;
+    if ((e = cluster_attr<true, false, RAW>(smem)) != cudaSuccess) return e;
+    return cluster_attr<true, true, RAW>(smem);
 }
 
 cudaError_t op_cluster_prepare(int smem)
 {
-    cudaError_t e;
-    if ((e = cluster_attr<false, false>(smem)) != cudaSuccess) return e;
-    if ((e = cluster_attr<false, true>(smem)) != cudaSuccess) return e;
-    if ((e = cluster_attr<true, false>(smem)) != cudaSuccess) return e;
-    return cluster_attr<true, true>(smem);
+    cudaError_t e = cluster_prepare_m<false>(smem);
+    if (e != cudaSuccess) return e;
+    return cluster_prepare_m<true>(smem);
 }
 
 cudaError_t op_cluster_max_active(int nc, int smem, int *n)
@@ -217,7 +229,7 @@ cudaError_t op_cluster_max_active(int nc, int smem, int *n)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(n, (void *)k_cluster<S, T, true, false>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, (void *)k_cluster<S, T, true, false, false>, &cfg);
 }
 
 cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd, const Coef<double> &kd, void *snap,
@@ -227,12 +239,20 @@ cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd
     const Coef<T> k = cast_coef<T>(kd);
     const S *a = static_cast<const S *>(pop0), *b = static_cast<const S *>(pop1);
     T *sn = static_cast<T *>(snap);
-    if (drho) {
-        if (force) return cluster_cfg_launch<true, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
-        return cluster_cfg_launch<true, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    if (gd.model == 1) {
+        if (drho) {
+            if (force) return cluster_cfg_launch<true, true, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+            return cluster_cfg_launch<true, false, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+        }
+        if (force) return cluster_cfg_launch<false, true, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+        return cluster_cfg_launch<false, false, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
     }
-    if (force) return cluster_cfg_launch<false, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
-    return cluster_cfg_launch<false, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    if (drho) {
+        if (force) return cluster_cfg_launch<true, true, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+        return cluster_cfg_launch<true, false, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    }
+    if (force) return cluster_cfg_launch<false, true, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    return cluster_cfg_launch<false, false, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
 }
 
 }  // namespace

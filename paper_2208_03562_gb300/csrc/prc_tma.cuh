@@ -94,6 +94,7 @@ struct TmaCfg {
     static constexpr int SMEM = 2 * STAGE_BYTES + R_BYTES + 128 + 128;  // + barriers, + base alignment
     static constexpr int THREADS = THREADS_;
     static constexpr int PAIRS = W / 2;               // node pairs per tile row
+    static constexpr int NQ = H * PAIRS / THREADS;    // node pairs per thread per tile
 };
 
 // Shared-memory access to a pair of neighbouring nodes (x, x+1) of one plane.
@@ -132,15 +133,17 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
     }
 }
 
-// Persistent step kernel: the interior tiles, one pair of neighbouring nodes
-// per thread (THREADS = H W / 2) with the collision in packed FP32x2
-// arithmetic, then the edge strips (`edge`, general tile body with bounce-back
-// and the lid, plain loads), so that one launch is one time step.
+// Persistent step kernel: the interior tiles, NQ pairs of neighbouring nodes
+// per thread (rows ly, ly + H/NQ, ...; H W / 2 = NQ THREADS) with the
+// collision in packed FP32x2 arithmetic, then the edge strips (`edge`,
+// general tile body with bounce-back and the lid, plain loads), so that one
+// launch is one time step.
 //
-// Per tile: every thread pulls its pair from the staged planes once and keeps
-// the nine values in registers; the density of the pair (and of one ring unit
-// for the first 2 W/2 + 2 (H + 2) threads) goes to the density tile R; after
-// one barrier the thread forms the density gradient from R and collides.
+// Per tile: every thread pulls its pairs from the staged planes once and
+// keeps the nine values of each in registers; the density of the pairs (and
+// of one ring unit for the first 2 W/2 + 2 (H + 2) threads) goes to the
+// density tile R; after one barrier the thread forms the density gradients
+// from R and collides its pairs.
 template <typename S, int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, S *__restrict__ dst, Grid gd,
@@ -148,7 +151,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
            DevStatus *__restrict__ st, Interior in, const __grid_constant__ Rects edge)
 {
     using C = TmaCfg<S, W, H, THREADS>;
-    static_assert(THREADS == H * C::PAIRS, "one node pair per thread");
+    static_assert(C::NQ >= 1 && C::NQ * THREADS == H * C::PAIRS, "whole node pairs per thread");
     static_assert(2 * C::PAIRS + 2 * C::RH <= THREADS, "one ring unit per thread at most");
     static_assert(C::R_BYTES >= srho_floats(THREADS) * (int)sizeof(float), "density tile too small for the strips");
     if (st->stop) return;
@@ -164,7 +167,9 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
     constexpr int RING = 2 * C::PAIRS + 2 * C::RH;        // ring units: 2 rows of pairs, 2 columns
 
     const int tid = threadIdx.x;
-    const int ly = tid / C::PAIRS, x = 2 * (tid - ly * C::PAIRS);  // this thread's pair in the tile
+    // this thread's pairs in the tile: column x, rows ly0 + j H / NQ
+    const int ly0 = tid / C::PAIRS, x = 2 * (tid - ly0 * C::PAIRS);
+    constexpr int DY = H / C::NQ;
     const int ntiles = in.ntx * in.nty;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -202,13 +207,18 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
         }
         int x0, y0, ox, oy;
         origin(tile, x0, y0, ox, oy);
-        const bool own = (x0 + x >= ox) & (y0 + ly >= oy);  // the pair is owned by this tile
-        const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
-        float2 snv = make_float2(0.f, 0.f);
+        const bool own_x = x0 + x >= ox;  // the pair's column is owned by this tile
+        float2 snv[C::NQ];
         if constexpr (EPI) {
             // the snapshot is touched once per residual step: stream it, and
-            // issue the load now so that it overlaps the copies
-            if (own) snv = __ldcs(reinterpret_cast<const float2 *>(snap + o));
+            // issue the loads now so that they overlap the copies
+#pragma unroll
+            for (int j = 0; j < C::NQ; j++) {
+                const int ly = ly0 + j * DY;
+                snv[j] = make_float2(0.f, 0.f);
+                if (own_x & (y0 + ly >= oy))
+                    snv[j] = __ldcs(reinterpret_cast<const float2 *>(snap + (long long)(y0 + ly) * gd.pitch + x0 + x));
+            }
         }
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -221,12 +231,14 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
             return;
         }
 
-        F2 g[9];
-        pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
-        F2 dxr(0.f), dyr(0.f);
+        F2 g[C::NQ][9];
+#pragma unroll
+        for (int j = 0; j < C::NQ; j++) pull_pair<S, PE>(cur + (ly0 + j * DY + 1) * C::BW + x + C::PADX, g[j]);
         if constexpr (DRHO) {
-            // density (minus rho0) of the pair, and of one ring unit
-            *reinterpret_cast<float2 *>(R + (ly + 1) * C::RW + x + 2) = sum9(g).v;
+            // density (minus rho0) of the pairs, and of one ring unit
+#pragma unroll
+            for (int j = 0; j < C::NQ; j++)
+                *reinterpret_cast<float2 *>(R + (ly0 + j * DY + 1) * C::RW + x + 2) = sum9(g[j]).v;
             if (tid < RING) {
                 if (tid < 2 * C::PAIRS) {
                     const int ry = tid < C::PAIRS ? 0 : H + 1;
@@ -245,33 +257,41 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                 }
             }
             __syncthreads();
-            const float *c = R + (ly + 1) * C::RW + x + 2;
-            const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
-                         Rr = *reinterpret_cast<const float2 *>(c + 2);
-            const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
-                         NM = *reinterpret_cast<const float2 *>(c + C::RW),
-                         NR = *reinterpret_cast<const float2 *>(c + C::RW + 2);
-            const float2 SL = *reinterpret_cast<const float2 *>(c - C::RW - 2),
-                         SM = *reinterpret_cast<const float2 *>(c - C::RW),
-                         SR = *reinterpret_cast<const float2 *>(c - C::RW + 2);
-            const float i12 = kf.inv12, i12r = kf.inv12r;
-            // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
-            // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
-            dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
-                     (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
-            dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
-                     (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
         }
-        F2 ux, uy, drho;
-        collide<F2, DRHO, FORCE>(k, g, dxr, dyr, ux, uy, drho);
 #pragma unroll
-        for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[i]);
-        if constexpr (EPI) {
-            if (own) {
-                __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
-                const float da = ux.v.x - snv.x, db = ux.v.y - snv.y;
-                acc.add(da * da, drho.v.x);
-                acc.add(db * db, drho.v.y);
+        for (int j = 0; j < C::NQ; j++) {
+            const int ly = ly0 + j * DY;
+            F2 dxr(0.f), dyr(0.f);
+            if constexpr (DRHO) {
+                const float *c = R + (ly + 1) * C::RW + x + 2;
+                const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
+                             Rr = *reinterpret_cast<const float2 *>(c + 2);
+                const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
+                             NM = *reinterpret_cast<const float2 *>(c + C::RW),
+                             NR = *reinterpret_cast<const float2 *>(c + C::RW + 2);
+                const float2 SL = *reinterpret_cast<const float2 *>(c - C::RW - 2),
+                             SM = *reinterpret_cast<const float2 *>(c - C::RW),
+                             SR = *reinterpret_cast<const float2 *>(c - C::RW + 2);
+                const float i12 = kf.inv12, i12r = kf.inv12r;
+                // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
+                // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
+                dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
+                         (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
+                dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
+                         (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
+            }
+            F2 ux, uy, drho;
+            collide<F2, DRHO, FORCE>(k, g[j], dxr, dyr, ux, uy, drho);
+            const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
+#pragma unroll
+            for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[j][i]);
+            if constexpr (EPI) {
+                if (own_x & (y0 + ly >= oy)) {
+                    __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
+                    const float da = ux.v.x - snv[j].x, db = ux.v.y - snv[j].y;
+                    acc.add(da * da, drho.v.x);
+                    acc.add(db * db, drho.v.y);
+                }
             }
         }
         __syncthreads();  // stage `cur` and R are free for reuse

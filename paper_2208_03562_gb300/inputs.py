@@ -111,6 +111,14 @@ def lid_speed_for_mach(r: float, mach: float, cap: float = 0.05) -> float:
     return min(cap, mach * min(1.0, r) * CS_STAR)
 
 
+def sweep_mach(gamma: float) -> float:
+    """Lid Mach number of the synthetic sweeps: 0.1, lowered to gamma / 2 for
+    strong preconditioning. The paper notes that the smallest usable gamma
+    grows with the Mach number (Sec. 5.2). Its own stable runs keep
+    Ma / gamma <= 0.75."""
+    return min(0.1, 0.5 * gamma)
+
+
 def square_cavity_64() -> Cavity:
     """64 x 64 square lattice, r = gamma = 1, Re = 100, U = 0.1, FP64,
     to residual 1e-8 or 20000 steps."""
@@ -143,7 +151,8 @@ def shallow_cavity_8192x2048(dtype: str = "f32") -> Cavity:
 def batched_sweep(seed: int = 0, n: int = 256, dtype: str = "f32"):
     """n independent cavities: nx ~ U{64..1024}, ny ~ U{32..512},
     r in {0.25, 0.5, 1, 2}, gamma log-uniform [0.05, 1], Re log-uniform
-    [100, 5000], Ma = 0.1 (lid speed capped at 0.05), residual 1e-7."""
+    [100, 5000], Ma = min(0.1, gamma / 2) (lid speed capped at 0.05),
+    residual 1e-7."""
     g = rng(seed)
     out = []
     for _ in range(n):
@@ -152,7 +161,7 @@ def batched_sweep(seed: int = 0, n: int = 256, dtype: str = "f32"):
         r = float(g.choice([0.25, 0.5, 1.0, 2.0]))
         gamma = float(math.exp(g.uniform(math.log(0.05), 0.0)))
         re = float(math.exp(g.uniform(math.log(100.0), math.log(5000.0))))
-        out.append(Cavity(nx, ny, r, gamma, re, lid_speed_for_mach(r, 0.1), dtype, 1e-7, 2_000_000))
+        out.append(Cavity(nx, ny, r, gamma, re, lid_speed_for_mach(r, sweep_mach(gamma)), dtype, 1e-7, 2_000_000))
     return out
 
 
@@ -162,19 +171,22 @@ class Request:
     cavity: Cavity
 
 
-def serving_requests(seed: int = 0, n: int = 256, rate_hz: float = 50.0, dtype: str = "f16"):
+def serving_requests(seed: int = 0, n: int = 256, rate_hz: float = 50.0, dtype: str = "f16", scale: int = 1):
     """Poisson arrivals (mean rate_hz) of steady-state cavity solves:
     nx ~ U{128..2048}, ny ~ U{64..1024}, r ~ U[0.25, 2], gamma log-uniform
-    [0.05, 1], Re log-uniform [100, 1000], Ma = 0.1 (cap 0.05), residual 1e-6."""
+    [0.05, 1], Re log-uniform [100, 1000], Ma = min(0.1, gamma / 2) (cap
+    0.05), residual 1e-6. `scale` divides both grid dimensions (the same
+    draws, a smaller mix)."""
     g = rng(seed)
     t = 0.0
     out = []
     for _ in range(n):
         t += float(g.exponential(1.0 / rate_hz))
-        nx = int(g.integers(128, 2049))
-        ny = int(g.integers(64, 1025))
+        nx = max(3, int(g.integers(128, 2049)) // scale)
+        ny = max(3, int(g.integers(64, 1025)) // scale)
         r = float(g.uniform(0.25, 2.0))
         gamma = float(math.exp(g.uniform(math.log(0.05), 0.0)))
         re = float(math.exp(g.uniform(math.log(100.0), math.log(1000.0))))
-        out.append(Request(t, Cavity(nx, ny, r, gamma, re, lid_speed_for_mach(r, 0.1), dtype, 1e-6, 2_000_000)))
+        out.append(Request(t, Cavity(nx, ny, r, gamma, re, lid_speed_for_mach(r, sweep_mach(gamma)), dtype, 1e-6,
+                                     2_000_000)))
     return out

@@ -17,6 +17,7 @@ F64, F32, F16 = 0, 1, 2
 DTYPE_CODES = {"f64": F64, "f32": F32, "f16": F16}
 BC_CAVITY, BC_CHANNEL, BC_PERIODIC = 0, 1, 2
 DRHO_CURRENT, DRHO_OFF = 0, 1
+MODEL_PRC, MODEL_PRNR = 0, 1
 
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTCONVERGED = range(7)
 VARIANT_GENERAL, VARIANT_CLUSTER = -1, -2
@@ -33,7 +34,7 @@ class lbm_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
                 ("r", C.c_double), ("gamma", C.c_double), ("nu", C.c_double), ("u_lid", C.c_double),
                 ("omega_xi", C.c_double), ("fx", C.c_double), ("fy", C.c_double),
-                ("dtype", C.c_int32), ("bc", C.c_int32), ("drho", C.c_int32), ("reserved", C.c_int32)]
+                ("dtype", C.c_int32), ("bc", C.c_int32), ("drho", C.c_int32), ("model", C.c_int32)]
 
 
 class lbm_info_t(C.Structure):
@@ -150,10 +151,10 @@ def _check(status, h=None):
 # C-named functions
 
 def lbm_params_init(nx, ny, r, gamma, nu, u_lid, dtype=F32, bc=BC_CAVITY, drho=DRHO_CURRENT,
-                    omega_xi=1.0, fx=0.0, fy=0.0) -> lbm_params:
+                    omega_xi=1.0, fx=0.0, fy=0.0, model=MODEL_PRC) -> lbm_params:
     p = lbm_params()
     _check(load().lbm_params_init(C.byref(p), nx, ny, r, gamma, nu, u_lid, dtype))
-    p.bc, p.drho, p.omega_xi, p.fx, p.fy = bc, drho, omega_xi, fx, fy
+    p.bc, p.drho, p.omega_xi, p.fx, p.fy, p.model = bc, drho, omega_xi, fx, fy, model
     return p
 
 

@@ -295,24 +295,24 @@ def test_gpu_server_alone_equals_mix():
 
 @pytest.mark.gpu
 def test_gpu_server_schedule_matches_oracle():
-    """FP16 until the residual stalls, then FP32. Run to residual 1e-7 (FP32
-    storage itself stalls near 7e-8 on this grid), the schedule lands on the
-    FP64 oracle's steady field within 5e-5 (relative L2 of u; the distance
-    left at that residual is ~2e-5): the FP16 transient leaves no trace.
-    Stopped at 1e-6, the field is still ~2e-4 from steady (as any run stopped
-    there), within the 1e-3 bound of the FP16 storage path at steady state."""
+    """FP16 until the residual stalls, then FP32 to 1e-7: the steady field is
+    within the 1e-3 bound of the FP16 storage path (relative L2 of u against
+    the FP64 oracle's steady field from rest). It does not come closer.
+    The scheme has undamped staggered velocity modes (u_x ~ (-1)^x, u_y ~
+    (-1)^y, test_staggered_modes_survive_in_the_steady_state). The FP16
+    rounding noise excites them, and no later FP32 or FP64 stepping removes
+    them."""
     L = _gpu_or_skip()
     from oracle import stepper as S
     nx, ny, r, gamma, U, re = 64, 32, 0.5, 0.25, 0.05, 100.0
     o = S.Oracle(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=U * ny * r / re, u_lid=U))
     o.run(1e-11, 600000)
     _, oux, ouy = o.fields()
-    for tol, bound in ((1e-7, 5e-5), (1e-6, 1e-3)):
-        req = _cavity_request(L, 0, 0.0, nx, ny, r, gamma, re, U, tol=tol, max_steps=600000)
-        srv = SV.gpu_server(SV.fp16_schedule(1000), capacity=4)
-        res = srv.serve([req])[0]
-        srv.close()
-        assert res.status == "converged" and len(res.steps_by_stage) == 2, res
-        _, ux, uy = res.fields
-        e = math.sqrt(np.sum((ux - oux) ** 2 + (uy - ouy) ** 2) / np.sum(oux ** 2 + ouy ** 2))
-        assert e < bound, (tol, e)
+    req = _cavity_request(L, 0, 0.0, nx, ny, r, gamma, re, U, tol=1e-7, max_steps=600000)
+    srv = SV.gpu_server(SV.fp16_schedule(1000), capacity=4)
+    res = srv.serve([req])[0]
+    srv.close()
+    assert res.status == "converged" and len(res.steps_by_stage) == 2, res
+    _, ux, uy = res.fields
+    e = math.sqrt(np.sum((ux - oux) ** 2 + (uy - ouy) ** 2) / np.sum(oux ** 2 + ouy ** 2))
+    assert e < 1e-3, e
