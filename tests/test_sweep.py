@@ -49,9 +49,10 @@ def test_centreline_profiles_pick_the_middle():
 @pytest.mark.gpu
 def test_preconditioning_cuts_steps_and_keeps_the_steady_field():
     """Shallow cavity of Sec. 5.2 (r = 0.2, 100 x 125, Re = 100, Ma = 0.06)
-    to residual 1e-6. Fewer steps the smaller gamma (about x3 at gamma = 0.1
-    at this residual; the reduction grows as the residual target tightens), and
-    the same steady field for every gamma."""
+    to residual 1e-6. The smaller gamma, the fewer steps (about x3 at
+    gamma = 0.1 at this residual; the reduction grows as the residual target
+    tightens). The steady field is the same for every gamma up to O(Ma^2 /
+    gamma)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
@@ -62,8 +63,11 @@ def test_preconditioning_cuts_steps_and_keeps_the_steady_field():
     steps = [r["steps"] for r in runs]
     assert steps[0] > steps[1] > steps[2], steps
     assert runs[2]["step_reduction_vs_gamma1"] > 2.5, steps
+    # the steady states of the preconditioned equations coincide up to the
+    # weak-compressibility error: p = gamma c_s^2 rho makes density
+    # variations 1/gamma larger, an O(Ma^2 / gamma) effect (0.0036 / gamma)
     _, u1, v1 = runs[0]["fields"]
     for r in runs[1:]:
         _, u2, v2 = r["fields"]
         rel = math.sqrt(np.sum((u1 - u2) ** 2 + (v1 - v2) ** 2) / np.sum(u1 ** 2 + v1 ** 2))
-        assert rel < 2e-3, (r["gamma"], rel)
+        assert rel < 0.006 / r["gamma"], (r["gamma"], rel)
