@@ -197,14 +197,19 @@ def gpu_leg(cav_dtype, steps, warmup, torch, L, dist=None, clocks_index=None):
         sampler.__exit__()
     ms = t0.elapsed_time(t1)
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, torch, "cuda")
         dist.barrier()
     info = g.info()
     launch = launch_times(g, min(steps, 200), torch)
     g.close()
     return cav, ms, info, (sampler.summary() if sampler else None), tuned, launch
+
+
+def max_over_ranks(value, dist, torch, device):
+    """The largest of every rank's `value` (a time), on every rank."""
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def launch_times(g, n, torch):
