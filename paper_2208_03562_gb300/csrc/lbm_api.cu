@@ -317,13 +317,17 @@ lbm_status cluster_select(lbm_t h, prc::ClusterGeom &g)
     int optin = 0;
     CK(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     const int budget = optin - 1024;  // static shared memory of the kernel
+    // The opt-in limit is an attribute of the kernel, shared by every handle
+    // in the process: it is set to the whole budget (the same value from any
+    // handle), never to this grid's size, which would make the launches of an
+    // earlier handle with larger slabs fail.
+    CK(h, h->ops->cluster_prepare(budget));
     for (int nc = prc::CL_MAX_CTAS; nc >= 1; nc--) {
         const int rpc = (h->p.ny + nc - 1) / nc;
         const int last = h->p.ny - (nc - 1) * rpc;
         if (rpc < 2 || last < 2) continue;
         const size_t smem = prc::cluster_smem_bytes(rpc, h->p.nx, h->ops->elem, h->ops->snap_elem);
         if (smem > (size_t)budget) continue;
-        CK(h, h->ops->cluster_prepare((int)smem));
         int active = 0;
         if (h->ops->cluster_max_active(nc, (int)smem, &active) != cudaSuccess) {
             cudaGetLastError();

@@ -81,10 +81,12 @@ def _lib():
     return L
 
 
-def solve(nx, ny, r, gamma, nu, u_lid, tol, max_steps, dtype="f32", want_fields=False, time_limit_s=None):
-    """One steady-state solve from rest; returns a result dict."""
+def solve(nx, ny, r, gamma, nu, u_lid, tol, max_steps, dtype="f32", want_fields=False, time_limit_s=None,
+          model=0):
+    """One steady-state solve from rest; returns a result dict. model 0 is
+    the central-moment scheme (PRC-LBM), 1 the raw-moment one (PRNR-LBM)."""
     L = _lib()
-    p = L.lbm_params_init(nx, ny, r, gamma, nu, u_lid, L.DTYPE_CODES[dtype])
+    p = L.lbm_params_init(nx, ny, r, gamma, nu, u_lid, L.DTYPE_CODES[dtype], model=model)
     h = L.Lbm(p)
     t0 = time.perf_counter()
     steps, status = 0, None
@@ -99,7 +101,7 @@ def solve(nx, ny, r, gamma, nu, u_lid, tol, max_steps, dtype="f32", want_fields=
     except L.LbmError as e:
         status = e.status
     wall = time.perf_counter() - t0
-    out = {"gamma": gamma, "steps": steps, "wall_s": wall, "variant": h.variant,
+    out = {"gamma": gamma, "model": model, "steps": steps, "wall_s": wall, "variant": h.variant,
            "status": {L.OK: "converged", L.EDIVERGED: "diverged"}.get(status, "not converged"),
            "residual": h.info().residual}
     if want_fields and out["status"] != "diverged":
@@ -109,24 +111,25 @@ def solve(nx, ny, r, gamma, nu, u_lid, tol, max_steps, dtype="f32", want_fields=
 
 
 def convergence_study(exp: Experiment, tol: float = 1e-6, max_steps: int = 20_000_000, dtype: str = "f32",
-                      workers: int = 8, want_fields: bool = False, time_limit_s: float = None) -> dict:
+                      workers: int = 8, want_fields: bool = False, time_limit_s: float = None,
+                      model: int = 0) -> dict:
     """Steps to `tol` for every gamma of an experiment, solved concurrently."""
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         futs = {g: ex.submit(solve, exp.nx, exp.ny, exp.r, g, exp.nu, exp.u_lid, tol, max_steps, dtype,
-                             want_fields, time_limit_s) for g in exp.gammas}
+                             want_fields, time_limit_s, model) for g in exp.gammas}
         runs = {g: f.result() for g, f in futs.items()}
     base = runs.get(1.0)
     for g, r in runs.items():
         if base and base["status"] == "converged" and r["status"] == "converged":
             r["step_reduction_vs_gamma1"] = base["steps"] / r["steps"]
-    return {"experiment": exp.name, "where": exp.where, "nx": exp.nx, "ny": exp.ny, "r": exp.r, "re": exp.re,
+    return {"experiment": exp.name, "model": model, "where": exp.where, "nx": exp.nx, "ny": exp.ny, "r": exp.r, "re": exp.re,
             "mach": exp.mach, "u_lid": exp.u_lid, "nu": exp.nu, "tol": tol, "dtype": dtype,
             "runs": [runs[g] for g in exp.gammas],
             "paper_context": {"steps": exp.paper_steps, "reduction": exp.paper_ratio}}
 
 
 def max_stable_re(nx, ny, r, gamma, u_lid, re_lo=50.0, re_hi=1e5, steps=200_000, iters=8, dtype="f32",
-                  tol=1e-9) -> dict:
+                  tol=1e-9, model=0) -> dict:
     """Largest Re (bisection in log Re) for which a run from rest stays finite
     for `steps` steps (or converges before), Sec. 5.3."""
     def stable(re):
@@ -136,26 +139,28 @@ def max_stable_re(nx, ny, r, gamma, u_lid, re_lo=50.0, re_hi=1e5, steps=200_000,
         w = 1.0 / (nu / (gamma * q * q / 3.0) + 0.5)
         if not (0.0 < w < 2.0):
             return False
-        return solve(nx, ny, r, gamma, nu, u_lid, tol, steps, dtype)["status"] != "diverged"
+        return solve(nx, ny, r, gamma, nu, u_lid, tol, steps, dtype, model=model)["status"] != "diverged"
     lo, hi = re_lo, re_hi
     if not stable(lo):
-        return {"gamma": gamma, "max_stable_re": None, "note": "unstable at the lower bracket"}
+        return {"gamma": gamma, "model": model, "max_stable_re": None, "note": "unstable at the lower bracket"}
     if stable(hi):
-        return {"gamma": gamma, "max_stable_re": hi, "note": "stable at the upper bracket"}
+        return {"gamma": gamma, "model": model, "max_stable_re": hi, "note": "stable at the upper bracket"}
     for _ in range(iters):
         mid = math.sqrt(lo * hi)
         if stable(mid):
             lo = mid
         else:
             hi = mid
-    return {"gamma": gamma, "max_stable_re": lo, "bracket": [lo, hi], "steps": steps}
+    return {"gamma": gamma, "model": model, "max_stable_re": lo, "bracket": [lo, hi], "steps": steps}
 
 
-def stability_study(gammas=(1.0, 0.5, 0.2), nx=100, ny=100, r=0.25, u_lid=0.02, steps=200_000, workers=4,
-                    dtype="f32") -> dict:
-    """Sec. 5.3: AR = 0.25 cavity, r = 0.25, U = 0.02; max stable Re per gamma."""
+def stability_study(gammas=(1.0, 0.5, 0.2), nx=100, ny=100, r=0.25, u_lid=0.02, steps=200_000, workers=6,
+                    dtype="f32", models=(0, 1)) -> dict:
+    """Sec. 5.3: AR = 0.25 cavity, r = 0.25, U = 0.02; max stable Re per
+    gamma, for the central-moment (0) and raw-moment (1) schemes."""
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = [ex.submit(max_stable_re, nx, ny, r, g, u_lid, steps=steps, dtype=dtype) for g in gammas]
+        futs = [ex.submit(max_stable_re, nx, ny, r, g, u_lid, steps=steps, dtype=dtype, model=m)
+                for m in models for g in gammas]
         res = [f.result() for f in futs]
     return {"where": "Sec. 5.3, stability", "nx": nx, "ny": ny, "r": r, "u_lid": u_lid, "steps": steps,
             "runs": res}

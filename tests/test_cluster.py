@@ -106,3 +106,24 @@ def test_cluster_autotune_restores_state():
     best, ms = h.autotune(20)
     assert len(ms) == L.lbm_variant_count(L.F32) + 1 and ms[-1] > 0
     assert np.array_equal(h.populations(), before) and h.info().step == 33
+
+
+@pytest.mark.parametrize("model", [L.MODEL_PRC, L.MODEL_PRNR])
+def test_handles_of_different_sizes_coexist(model):
+    """The engine's shared-memory opt-in is a property of the kernel, not of a
+    handle: creating a handle with smaller slabs (and of either scheme) after
+    one with larger slabs must leave the larger one runnable."""
+    def mk(nx, ny, m):
+        h = L.Lbm(L.lbm_params_init(nx, ny, 4.0 / 3.0, 0.5, 0.007, 0.0346, L.F32, model=m))
+        assert h.variant == L.VARIANT_CLUSTER
+        return h
+    big = mk(100, 150, L.MODEL_PRC)
+    small = mk(100, 125, model)
+    big.step(40)
+    small.step(40)
+    big.step(40)
+    ref = mk(100, 150, L.MODEL_PRC)
+    ref.step(80)
+    assert np.array_equal(big.populations(), ref.populations())
+    for h in (big, small, ref):
+        h.close()
