@@ -91,7 +91,7 @@ struct TmaCfg {
     static constexpr int STAGE_BYTES = 9 * PLANE_BYTES;
     static constexpr int RW = W + 4, RH = H + 2;      // density tile: node lx at column lx + 2
     static constexpr int R_BYTES = (RW * RH * 4 + 127) / 128 * 128;
-    static constexpr int SMEM = 2 * STAGE_BYTES + R_BYTES + 128 + 128;  // + barriers, + base alignment
+    static constexpr int SMEM = 2 * STAGE_BYTES + 2 * R_BYTES + 128 + 128;  // two density tiles, + barriers, + base alignment
     static constexpr int THREADS = THREADS_;
     static constexpr int PAIRS = W / 2;               // node pairs per tile row
     static constexpr int NQ = H * PAIRS / THREADS;    // node pairs per thread per tile
@@ -142,8 +142,14 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
 // Per tile: every thread pulls its pairs from the staged planes once and
 // keeps the nine values of each in registers; the density of the pairs (and
 // of one ring unit for the first 2 W/2 + 2 (H + 2) threads) goes to the
-// density tile R; after one barrier the thread forms the density gradients
-// from R and collides its pairs.
+// density tile R[it & 1]; after one barrier the thread forms the density
+// gradients from R[it & 1] and collides its pairs.  That barrier is the only
+// one per tile: after it the stage just read is free, so thread 0 refills it
+// with the copies of the tile after next (two tiles in flight during the
+// collision), and the density tile alternates between two buffers, so a
+// thread may start the next tile while others still read this tile's
+// densities (the next write of R[it & 1] comes after the next barrier, which
+// every thread reaches only once its collision of this tile is done).
 template <typename S, int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, S *__restrict__ dst, Grid gd,
@@ -162,7 +168,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
     S *stage0 = reinterpret_cast<S *>(smem);
     S *stage1 = reinterpret_cast<S *>(smem + C::STAGE_BYTES);
     float *R = reinterpret_cast<float *>(smem + 2 * C::STAGE_BYTES);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE_BYTES + C::R_BYTES);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE_BYTES + 2 * C::R_BYTES);
+    constexpr int RF = C::R_BYTES / (int)sizeof(float);  // floats per density tile
     constexpr int PE = C::PLANE_BYTES / (int)sizeof(S);  // plane stride in elements
     constexpr int RING = 2 * C::PAIRS + 2 * C::RH;        // ring units: 2 rows of pairs, 2 columns
 
@@ -194,17 +201,15 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
 
     RedAcc<float> acc;
     int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) issue(tile, stage0, &bar[0]);
-    bool in_flight_other = false;  // (thread 0) a copy into the other stage is outstanding
+    if (tid == 0) {
+        if (tile < ntiles) issue(tile, stage0, &bar[0]);
+        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, stage1, &bar[1]);
+    }
     int it = 0;
     for (; tile < ntiles; it++, tile += gridDim.x) {
         const int s = it & 1;
-        const S *cur = s ? stage1 : stage0;
-        const int next = tile + gridDim.x;
-        if (tid == 0) {
-            in_flight_other = next < ntiles;
-            if (in_flight_other) issue(next, s ? stage0 : stage1, &bar[s ^ 1]);
-        }
+        S *cur = s ? stage1 : stage0;
+        float *Rs = R + s * RF;
         int x0, y0, ox, oy;
         origin(tile, x0, y0, ox, oy);
         const bool own_x = x0 + x >= ox;  // the pair's column is owned by this tile
@@ -225,7 +230,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
             if (tid == 0) {
                 atomicExch(&st->timeout, 1);
                 atomicExch(&st->stop, 1);
-                if (in_flight_other) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+                // the copies of the next tile into the other stage may be outstanding
+                if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
             }
             __syncthreads();
             return;
@@ -238,32 +244,35 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
             // density (minus rho0) of the pairs, and of one ring unit
 #pragma unroll
             for (int j = 0; j < C::NQ; j++)
-                *reinterpret_cast<float2 *>(R + (ly0 + j * DY + 1) * C::RW + x + 2) = sum9(g[j]).v;
+                *reinterpret_cast<float2 *>(Rs + (ly0 + j * DY + 1) * C::RW + x + 2) = sum9(g[j]).v;
             if (tid < RING) {
                 if (tid < 2 * C::PAIRS) {
                     const int ry = tid < C::PAIRS ? 0 : H + 1;
                     const int rx = 2 * (tid < C::PAIRS ? tid : tid - C::PAIRS);
                     F2 gr[9];
                     pull_pair<S, PE>(cur + ry * C::BW + rx + C::PADX, gr);
-                    *reinterpret_cast<float2 *>(R + ry * C::RW + rx + 2) = sum9(gr).v;
+                    *reinterpret_cast<float2 *>(Rs + ry * C::RW + rx + 2) = sum9(gr).v;
                 } else {
                     const int c = tid - 2 * C::PAIRS;
                     const int ry = c >> 1, lx = (c & 1) ? W : -1;
                     const S *b = cur + ry * C::BW + lx + C::PADX;
-                    float sum = 0.f;
+                    float gr[9];
 #pragma unroll
-                    for (int i = 0; i < 9; i++) sum += Pair<S>::one(b + i * PE - ex_of(i));
-                    R[ry * C::RW + lx + 2] = sum;
+                    for (int i = 0; i < 9; i++) gr[i] = Pair<S>::one(b + i * PE - ex_of(i));
+                    // same summation order as every other density, so a node's
+                    // density does not depend on which tile formed it
+                    Rs[ry * C::RW + lx + 2] = sum9(gr);
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();  // every pull from `cur` is done and R[s] is complete
+        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, cur, &bar[s]);
 #pragma unroll
         for (int j = 0; j < C::NQ; j++) {
             const int ly = ly0 + j * DY;
             F2 dxr(0.f), dyr(0.f);
             if constexpr (DRHO) {
-                const float *c = R + (ly + 1) * C::RW + x + 2;
+                const float *c = Rs + (ly + 1) * C::RW + x + 2;
                 const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
                              Rr = *reinterpret_cast<const float2 *>(c + 2);
                 const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
@@ -294,9 +303,9 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                 }
             }
         }
-        __syncthreads();  // stage `cur` and R are free for reuse
     }
-    // edge strips: general tile body, density tile in R (free now)
+    __syncthreads();  // every collision is done: R is free
+    // edge strips: general tile body, density tile in R
     for (int e = blockIdx.x; e < edge.start[edge.n]; e += gridDim.x) {
         int ex0, ey0, ex1, ey1, lw;
         rect_tile(edge, e, ex0, ey0, ex1, ey1, lw);
