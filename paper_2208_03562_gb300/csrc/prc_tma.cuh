@@ -205,13 +205,23 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
         if (tile < ntiles) issue(tile, stage0, &bar[0]);
         if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, stage1, &bar[1]);
     }
+    // tile coordinates of this CTA's current tile, advanced by gridDim.x
+    // tiles per iteration without a division
+    int tcx = blockIdx.x % in.ntx, tcy = blockIdx.x / in.ntx;
+    const int sdx = gridDim.x % in.ntx, sdy = gridDim.x / in.ntx;
     int it = 0;
     for (; tile < ntiles; it++, tile += gridDim.x) {
         const int s = it & 1;
         S *cur = s ? stage1 : stage0;
         float *Rs = R + s * RF;
-        int x0, y0, ox, oy;
-        origin(tile, x0, y0, ox, oy);
+        const int ox = in.ix0 + tcx * W, oy = in.iy0 + tcy * H;
+        const int x0 = min(ox, in.xlast), y0 = min(oy, in.ylast);
+        tcx += sdx;
+        tcy += sdy;
+        if (tcx >= in.ntx) {
+            tcx -= in.ntx;
+            tcy++;
+        }
         const bool own_x = x0 + x >= ox;  // the pair's column is owned by this tile
         float2 snv[C::NQ];
         if constexpr (EPI) {
@@ -225,17 +235,11 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                     snv[j] = __ldcs(reinterpret_cast<const float2 *>(snap + (long long)(y0 + ly) * gd.pitch + x0 + x));
             }
         }
+        // A thread whose wait runs out still pulls (stale shared memory, no
+        // harm) so that every thread reaches the one barrier of the tile,
+        // which also takes the vote: on a timeout anywhere the CTA leaves
+        // there, before any store of this tile.
         const bool ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(&st->timeout, 1);
-                atomicExch(&st->stop, 1);
-                // the copies of the next tile into the other stage may be outstanding
-                if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
-            }
-            __syncthreads();
-            return;
-        }
 
         F2 g[C::NQ][9];
 #pragma unroll
@@ -265,7 +269,16 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                 }
             }
         }
-        __syncthreads();  // every pull from `cur` is done and R[s] is complete
+        // every pull from `cur` is done and R[s] is complete
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(&st->timeout, 1);
+                atomicExch(&st->stop, 1);
+                // the copies of the next tile into the other stage may be outstanding
+                if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+            return;
+        }
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, cur, &bar[s]);
 #pragma unroll
         for (int j = 0; j < C::NQ; j++) {
