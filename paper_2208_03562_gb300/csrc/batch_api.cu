@@ -305,7 +305,8 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         I.pop[1] = slot_pop(sl, 1);
         I.snap = slot_snap(sl);
         I.gd = sl.gd;
-        I.tiles_x = ceil_div(sl.p.nx, prc::BX);
+        // the tile shape of k_batch: 64 x 8 (pairs, FP32 collision) or 32 x 8 (FP64)
+        I.tiles_x = ceil_div(sl.p.nx, sl.p.dtype == LBM_F64 ? prc::BX : prc::PTW);
         I.tiles = I.tiles_x * ceil_div(sl.p.ny, prc::BY);
         I.tile_start = tiles;
         I.part_base = tiles;

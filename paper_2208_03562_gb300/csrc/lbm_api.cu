@@ -1003,9 +1003,10 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params *p, const void *src, voi
     if (with_residual && !out) return fail(nullptr, LBM_EINVAL, "null residual output");
     if (src == dst) return fail(nullptr, LBM_EINVAL, "src and dst must be different buffers");
     const Plan pl = make_plan(*p, 0, -1);  // general kernel over the whole grid
-    if (pl.nparts > NOALLOC_MAX_PARTS)
+    const long long cells = (long long)((p->nx + 31) / 32) * (long long)((p->ny + 7) / 8);
+    if (cells > NOALLOC_MAX_PARTS || pl.nparts > NOALLOC_MAX_PARTS)
         return fail(nullptr, LBM_EINVAL,
-                    "grid too large for lbm_step_noalloc: ceil(nx/32)*ceil(ny/8) = " + std::to_string(pl.nparts) +
+                    "grid too large for lbm_step_noalloc: ceil(nx/32)*ceil(ny/8) = " + std::to_string(cells) +
                         " exceeds " + std::to_string(NOALLOC_MAX_PARTS));
     NoallocScratch sc;
     s = noalloc_scratch(&sc);

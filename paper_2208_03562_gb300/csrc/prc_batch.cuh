@@ -3,8 +3,8 @@
 // A batch is a table of instances, each with its own grid, parameters,
 // population sets, residual snapshot and step counter.  One cooperative launch
 // of k_batch advances every active instance by up to `steps` time steps: in
-// each step the CTAs sweep the BX x BY tiles of all active instances (general
-// wall-aware tile body), a grid barrier separates the steps, and after each
+// each step the CTAs sweep the tiles of all active instances (wall-aware tile
+// body: 64 x 8 nodes in pairs for the FP32 collision, 32 x 8 for FP64), a grid barrier separates the steps, and after each
 // residual step (every 20 steps of an instance's own counter) one CTA per
 // instance reduces that instance's per-tile partial sums in a fixed order,
 // so an instance's result does not depend on the other instances of the mix.
@@ -18,9 +18,24 @@
 // runs out it records LBM_ETIMEOUT and every CTA leaves.
 #pragma once
 
-#include "prc_kernels.cuh"
+#include <type_traits>
+
+#include "prc_pair.cuh"
 
 namespace prc {
+
+// Per-slot coefficient table entry: the collision constants in the collision
+// type and, for the FP32 collision, packed for the pair tile body.
+template <typename T>
+struct BatchCoef {
+    Coef<T> k;
+    Coef<F2> k2;
+};
+
+// Tile of the batch engine: 64 x 8 nodes (pair tile body) for the FP32
+// collision, 32 x 8 (one node per thread) for FP64.
+template <typename T>
+__host__ __device__ constexpr int batch_tile_w() { return std::is_same<T, float>::value ? PTW : BX; }
 
 enum BatchState : int {
     BATCH_ACTIVE = 0,
@@ -117,15 +132,24 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl)
 }
 
 template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool RAW>
-__device__ __forceinline__ void batch_tile_t(const BatchInst &I, const Coef<T> &k, int parity, int lt,
+__device__ __forceinline__ void batch_tile_t(const BatchInst &I, const BatchCoef<T> &k, int parity, int lt,
                                              double2 *partials)
 {
-    __shared__ T srho[srho_floats(BX * BY)];
-    const int x0 = (lt % I.tiles_x) * BX, y0 = (lt / I.tiles_x) * BY;
     RedAcc<T> acc;
-    general_tile<S, T, DRHO, EPI, FORCE, true, RAW>(static_cast<const S *>(I.pop[parity]),
-                                               static_cast<S *>(I.pop[parity ^ 1]), I.gd, k,
-                                               static_cast<T *>(I.snap), x0, y0, I.gd.nx, I.gd.ny, 5, acc, srho);
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ __align__(16) float srho[PAIR_SRHO];
+        const int x0 = (lt % I.tiles_x) * PTW, y0 = (lt / I.tiles_x) * PTH;
+        pair_tile<S, DRHO, EPI, FORCE, true, RAW>(static_cast<const S *>(I.pop[parity]),
+                                                 static_cast<S *>(I.pop[parity ^ 1]), I.gd, k.k, k.k2,
+                                                 static_cast<float *>(I.snap), x0, y0, acc, srho);
+    } else {
+        __shared__ T srho[srho_floats(BX * BY)];
+        const int x0 = (lt % I.tiles_x) * BX, y0 = (lt / I.tiles_x) * BY;
+        general_tile<S, T, DRHO, EPI, FORCE, true, RAW>(static_cast<const S *>(I.pop[parity]),
+                                                   static_cast<S *>(I.pop[parity ^ 1]), I.gd, k.k,
+                                                   static_cast<T *>(I.snap), x0, y0, I.gd.nx, I.gd.ny, 5, acc,
+                                                   srho);
+    }
     if constexpr (EPI) {
         __shared__ double red[2 * (BX * BY / 32)];
         double a, b;
@@ -136,7 +160,7 @@ __device__ __forceinline__ void batch_tile_t(const BatchInst &I, const Coef<T> &
 }
 
 template <typename S, typename T, bool RAW>
-__device__ __forceinline__ void batch_tile_m(const BatchInst &I, const Coef<T> &k, int parity, int lt, bool epi,
+__device__ __forceinline__ void batch_tile_m(const BatchInst &I, const BatchCoef<T> &k, int parity, int lt, bool epi,
                                              double2 *partials)
 {
     if (I.drho) {
@@ -159,7 +183,7 @@ __device__ __forceinline__ void batch_tile_m(const BatchInst &I, const Coef<T> &
 }
 
 template <typename S, typename T>
-__device__ __forceinline__ void batch_tile(const BatchInst &I, const Coef<T> &k, int parity, int lt, bool epi,
+__device__ __forceinline__ void batch_tile(const BatchInst &I, const BatchCoef<T> &k, int parity, int lt, bool epi,
                                            double2 *partials)
 {
     if (I.gd.model == 1) batch_tile_m<S, T, true>(I, k, parity, lt, epi, partials);
@@ -168,7 +192,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst &I, const Coef<T> &k,
 
 template <typename S, typename T>
 __global__ void __launch_bounds__(BX * BY)
-k_batch(const BatchInst *__restrict__ inst, const Coef<T> *__restrict__ coefs, BatchDyn *dyn, int ninst,
+k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coefs, BatchDyn *dyn, int ninst,
         int total_tiles, double2 *partials, BatchCtl *ctl, int steps)
 {
     const int tid = threadIdx.y * BX + threadIdx.x;

@@ -10,8 +10,10 @@
 //      shared memory through the cluster's distributed shared memory;
 //   2. CTA barrier;
 //   3. every slab node: pull, density gradient from the tile, collision
-//      (the same `collide` as every other kernel, so the populations are
-//      bitwise those of the general kernel), store into the other set;
+//      (the same `collide` as every other kernel, on pairs of neighbouring
+//      nodes in packed FP32x2 arithmetic for the FP32 collision, as in the
+//      general kernel, so the populations are bitwise those of the general
+//      kernel), store into the other set;
 //   4. cluster barrier: the new set is complete before anyone pulls from it.
 // Every 20th step of the absolute step counter the CTAs add their FP64
 // residual / mass totals in rank order (identically in every CTA, so the
@@ -22,6 +24,8 @@
 #pragma once
 
 #include <cooperative_groups.h>
+
+#include <type_traits>
 
 #include "prc_kernels.cuh"
 
@@ -129,8 +133,8 @@ __device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &
 // goes to pop_out[parity of that step].
 template <typename S, typename T, bool DRHO, bool FORCE, bool RAW>
 __global__ void __launch_bounds__(CL_THREADS, 1)
-k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<T> k, T *__restrict__ snap,
-          DevStatus *__restrict__ st, long long t0, int nsteps, int rpc)
+k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<T> k, Coef<F2> k2,
+          T *__restrict__ snap, DevStatus *__restrict__ st, long long t0, int nsteps, int rpc)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -209,6 +213,65 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
         }
         // 2. collide every slab node into the other set
         RedAcc<T> acc;
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 collision: pairs of neighbouring nodes (x, x + 1), x even,
+            // in packed FP32x2 arithmetic, as in the general kernel
+            const int npx = (nx + 1) >> 1, npairs = rows * npx;
+            const int p_dly = nthr / npx, p_dx = nthr - p_dly * npx;
+            int py = tid / npx, pxi = tid - py * npx;
+            for (int q = tid; q < npairs; q += nthr) {
+                const int ly = py, x = 2 * pxi;
+                pxi += p_dx;
+                py += p_dly;
+                if (pxi >= npx) {
+                    pxi -= npx;
+                    py++;
+                }
+                const int y = v.y_lo + ly;
+                const bool v1 = x + 1 < nx;
+                float ga[9], gb[9];
+                pull9_slab<S, float>(v, gd, x, y, k.lid, ga);
+                if (v1) pull9_slab<S, float>(v, gd, x + 1, y, k.lid, gb);
+                else
+#pragma unroll
+                    for (int i = 0; i < 9; i++) gb[i] = ga[i];
+                F2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; i++) g[i] = F2(ga[i], gb[i]);
+                float dx[2] = {0.f, 0.f}, dy[2] = {0.f, 0.f};
+                if constexpr (DRHO) {
+#pragma unroll
+                    for (int j = 0; j < 2; j++) {
+                        const float *c = rho + (ly + 1) * RW + x + j + 1;
+                        const float rE = c[1], rW = c[-1];
+                        const float rN = c[RW], rS = c[-RW];
+                        const float rNE = c[RW + 1], rNW = c[RW - 1];
+                        const float rSE = c[-RW + 1], rSW = c[-RW - 1];
+                        dx[j] = (float(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
+                        dy[j] = (float(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+                    }
+                }
+                F2 ux, uy, drho;
+                collide<F2, DRHO, FORCE, RAW>(k2, g, F2(dx[0], dx[1]), F2(dy[0], dy[1]), ux, uy, drho);
+                const long long o = (long long)ly * nx + x;
+#pragma unroll
+                for (int i = 0; i < 9; i++) {
+                    Fo[i * v.plane + o] = to_s<S, float>(g[i].v.x);
+                    if (v1) Fo[i * v.plane + o + 1] = to_s<S, float>(g[i].v.y);
+                }
+                if (epi) {
+                    const long long og = (long long)y * gd.pitch + x;
+                    const float d0 = ux.v.x - snap[og];
+                    snap[og] = ux.v.x;
+                    acc.add(d0 * d0, drho.v.x);
+                    if (v1) {
+                        const float d1 = ux.v.y - snap[og + 1];
+                        snap[og + 1] = ux.v.y;
+                        acc.add(d1 * d1, drho.v.y);
+                    }
+                }
+            }
+        } else {
         int sy_ = s_ly0, sx_ = s_x0;
         for (int q = tid; q < nslab; q += nthr) {
             const int ly = sy_, x = sx_;
@@ -242,6 +305,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 snap[og] = ux;
                 acc.add(d * d, drho);
             }
+        }
         }
         if (epi) {
             double a, bb;

@@ -104,7 +104,10 @@ inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
         add_strip(pl.edge, xend, iy0, p.nx, yend, threads);
         pl.n_edge_ctas = 0;  // the strips ride in the interior launch
     } else {
-        add_rect(pl.edge, 0, 0, p.nx, p.ny, 5, prc::BX * prc::BY);
+        // general kernel over the whole grid: 32 x 8 tiles of one node per
+        // thread (FP64), 64 x 8 tiles of node pairs (FP32 collision)
+        if (p.dtype == LBM_F64) add_rect(pl.edge, 0, 0, p.nx, p.ny, 5, prc::BX * prc::BY);
+        else add_rect(pl.edge, 0, 0, p.nx, p.ny, 6, prc::PTW * prc::PTH);  // 2^6 x (512 >> 6) nodes
         pl.n_edge_ctas = pl.edge.start[pl.edge.n];
     }
     pl.nparts = pl.n_int_ctas + pl.n_edge_ctas;

@@ -77,9 +77,21 @@ cudaError_t prepare_tma()
 }
 
 template <bool DRHO, bool EPI, bool FORCE>
-cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn,
+cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<double> &kd, T *sn,
                            double2 *partials, const DevStatus *st, cudaStream_t s)
 {
+    if constexpr (std::is_same<T, float>::value) {  // pair tile body, 64 x 8 tiles
+        const Coef<float> kf = cast_coef<float>(kd);
+        const Coef<F2> k2 = cast_coef<F2>(kd);
+        if (gd.model == 1)
+            k_step_pair<S, DRHO, EPI, FORCE, true><<<pl.n_edge_ctas, 256, 0, s>>>(a, b, gd, kf, k2, sn, partials, st,
+                                                                                 pl.edge, pl.n_int_ctas);
+        else
+            k_step_pair<S, DRHO, EPI, FORCE, false><<<pl.n_edge_ctas, 256, 0, s>>>(a, b, gd, kf, k2, sn, partials,
+                                                                                  st, pl.edge, pl.n_int_ctas);
+        return cudaGetLastError();
+    }
+    const Coef<T> k = cast_coef<T>(kd);
     if (gd.model == 1)
         k_step<S, T, DRHO, EPI, FORCE, true><<<pl.n_edge_ctas, dim3(BX, BY), 0, s>>>(a, b, gd, k, sn, partials, st,
                                                                                      pl.edge, pl.n_int_ctas);
@@ -90,7 +102,7 @@ cudaError_t launch_general(const S *a, S *b, const Plan &pl, const Grid &gd, con
 }
 
 template <bool DRHO, bool EPI>
-cudaError_t general_f(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<T> &k, T *sn, double2 *partials,
+cudaError_t general_f(const S *a, S *b, const Plan &pl, const Grid &gd, const Coef<double> &k, T *sn, double2 *partials,
                       const DevStatus *st, bool force, cudaStream_t s)
 {
     if (force) return launch_general<DRHO, EPI, true>(a, b, pl, gd, k, sn, partials, st, s);
@@ -101,19 +113,23 @@ cudaError_t op_step_general(const void *src, void *dst, const Plan &pl, const Gr
                             void *snap, double2 *partials, const DevStatus *st, bool drho, bool epi, bool force,
                             cudaStream_t s)
 {
-    const Coef<T> k = cast_coef<T>(kd);
     const S *a = static_cast<const S *>(src);
     S *b = static_cast<S *>(dst);
     T *sn = static_cast<T *>(snap);
     if (drho) {
-        if (epi) return general_f<true, true>(a, b, pl, gd, k, sn, partials, st, force, s);
-        return general_f<true, false>(a, b, pl, gd, k, sn, partials, st, force, s);
+        if (epi) return general_f<true, true>(a, b, pl, gd, kd, sn, partials, st, force, s);
+        return general_f<true, false>(a, b, pl, gd, kd, sn, partials, st, force, s);
     }
-    if (epi) return general_f<false, true>(a, b, pl, gd, k, sn, partials, st, force, s);
-    return general_f<false, false>(a, b, pl, gd, k, sn, partials, st, force, s);
+    if (epi) return general_f<false, true>(a, b, pl, gd, kd, sn, partials, st, force, s);
+    return general_f<false, false>(a, b, pl, gd, kd, sn, partials, st, force, s);
 }
 
-void op_coef_convert(const Coef<double> &in, void *out) { *static_cast<Coef<T> *>(out) = cast_coef<T>(in); }
+void op_coef_convert(const Coef<double> &in, void *out)
+{
+    BatchCoef<T> *c = static_cast<BatchCoef<T> *>(out);
+    c->k = cast_coef<T>(in);
+    c->k2 = cast_coef<F2>(in);
+}
 
 cudaError_t op_batch_occupancy(int *blocks_per_sm)
 {
@@ -124,7 +140,7 @@ cudaError_t op_batch_occupancy(int *blocks_per_sm)
 cudaError_t op_batch_launch(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int total_tiles,
                             double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s)
 {
-    const Coef<T> *cf = static_cast<const Coef<T> *>(coefs);
+    const BatchCoef<T> *cf = static_cast<const BatchCoef<T> *>(coefs);
     void *args[] = {(void *)&inst, (void *)&cf, (void *)&dyn, (void *)&ninst, (void *)&total_tiles,
                     (void *)&partials, (void *)&ctl, (void *)&steps};
     return cudaLaunchCooperativeKernel((const void *)k_batch<S, T>, dim3(grid), dim3(BX, BY), args, 0, s);
@@ -173,7 +189,8 @@ cudaError_t op_add_rest(void *pop, const Grid &gd, const Coef<double> &k, double
 }
 
 template <bool DRHO, bool FORCE, bool RAW>
-cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const Coef<T> &k, T *snap, DevStatus *st,
+cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const Coef<T> &k, const Coef<F2> &k2,
+                               T *snap, DevStatus *st,
                                long long t0, int n, int nc, int rpc, int smem, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
@@ -188,7 +205,7 @@ cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const C
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE, RAW>, p0, p1, gd, k, snap, st, t0, n, rpc);
+    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE, RAW>, p0, p1, gd, k, k2, snap, st, t0, n, rpc);
 }
 
 template <bool DRHO, bool FORCE, bool RAW>
@@ -237,22 +254,23 @@ cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd
                               cudaStream_t s)
 {
     const Coef<T> k = cast_coef<T>(kd);
+    const Coef<F2> k2 = cast_coef<F2>(kd);
     const S *a = static_cast<const S *>(pop0), *b = static_cast<const S *>(pop1);
     T *sn = static_cast<T *>(snap);
     if (gd.model == 1) {
         if (drho) {
-            if (force) return cluster_cfg_launch<true, true, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
-            return cluster_cfg_launch<true, false, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+            if (force) return cluster_cfg_launch<true, true, true>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
+            return cluster_cfg_launch<true, false, true>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
         }
-        if (force) return cluster_cfg_launch<false, true, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
-        return cluster_cfg_launch<false, false, true>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+        if (force) return cluster_cfg_launch<false, true, true>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
+        return cluster_cfg_launch<false, false, true>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
     }
     if (drho) {
-        if (force) return cluster_cfg_launch<true, true, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
-        return cluster_cfg_launch<true, false, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+        if (force) return cluster_cfg_launch<true, true, false>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
+        return cluster_cfg_launch<true, false, false>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
     }
-    if (force) return cluster_cfg_launch<false, true, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
-    return cluster_cfg_launch<false, false, false>(a, b, gd, k, sn, st, t0, n, nc, rpc, smem, s);
+    if (force) return cluster_cfg_launch<false, true, false>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
+    return cluster_cfg_launch<false, false, false>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
 }
 
 }  // namespace
@@ -261,7 +279,7 @@ cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd
     { W, H, THREADS, MINB, prepare_tma<W, H, THREADS, MINB>, launch_tma<W, H, THREADS, MINB> }
 
 const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), 16 / (int)sizeof(S), PRC_NVARIANTS, {PRC_VARIANTS},
-                          op_step_general, sizeof(Coef<T>), op_coef_convert, op_batch_occupancy, op_batch_launch,
+                          op_step_general, sizeof(BatchCoef<T>), op_coef_convert, op_batch_occupancy, op_batch_launch,
                           op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial, op_add_rest,
                           op_cluster_prepare, op_cluster_max_active, op_cluster_launch};
 

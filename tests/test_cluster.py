@@ -2,9 +2,10 @@
 
 One thread-block cluster keeps the whole state in distributed shared memory
 and runs many steps per launch. It performs the same per-node arithmetic as
-the general kernel, so its populations must be bitwise those of the general
-kernel, step for step, across wall types, the density-gradient mode, body
-forces and storage types. It must also stop on the device at the same step
+the general kernel (scalar FP64; pairs of neighbouring nodes in packed FP32x2
+for the FP32 collision), so its populations must be bitwise those of the
+general kernel, step for step, across wall types, the density-gradient mode,
+body forces and storage types. It must also stop on the device at the same step
 when run to a residual.
 """
 import numpy as np
