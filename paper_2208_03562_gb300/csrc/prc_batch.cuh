@@ -191,7 +191,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst &I, const BatchCoef<T
 }
 
 template <typename S, typename T>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 3)
 k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coefs, BatchDyn *dyn, int ninst,
         int total_tiles, double2 *partials, BatchCtl *ctl, int steps)
 {
