@@ -122,7 +122,8 @@ struct lbm_s {
     Plan plan;
     int variant;          // interior-kernel variant (-1: general kernel only)
     int num_sms;
-    CUtensorMap tmap[2];  // TMA descriptors of the two population sets
+    CUtensorMap tmap[2];     // TMA load descriptors of the two population sets (box = tile + ring)
+    CUtensorMap tmap_st[2];  // TMA store descriptors of the two sets (box = tile)
     prc::ClusterGeom cgeo;  // cluster-resident engine (variant LBM_VARIANT_CLUSTER)
     cudaGraphExec_t g20;
     bool have_g20;
@@ -179,7 +180,8 @@ lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
     const int c = (int)(t_before & 1);
     const bool drho = h->p.drho == LBM_DRHO_CURRENT, force = h->p.fx != 0.0 || h->p.fy != 0.0;
     if (h->plan.tma)
-        CK(h, h->ops->variants[h->variant].launch(&h->tmap[c], h->pop[c], h->pop[c ^ 1], h->plan, h->gd, h->k,
+        CK(h, h->ops->variants[h->variant].launch(&h->tmap[c], &h->tmap_st[c ^ 1], h->pop[c], h->pop[c ^ 1], h->plan,
+                                                   h->gd, h->k,
                                                    h->snap, h->partials, h->st, drho, epi, force, s));
     if (h->plan.n_edge_ctas > 0)
         CK(h, h->ops->step_general(h->pop[c], h->pop[c ^ 1], h->plan, h->gd, h->k, h->snap, h->partials, h->st,
@@ -277,8 +279,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// 3-D tiled descriptor over one population set: (x < nx, y < ny, plane < 9),
-// box = interior tile + ring, x widened to 16-byte aligned edges.
+// 3-D tiled descriptors over one population set: (x < nx, y < ny, plane < 9).
+// Load: box = interior tile + ring, x widened to 16-byte aligned edges.
+// Store: box = interior tile (its x origin is 16-byte aligned, and it lies
+// inside the grid, so no store starts at a negative coordinate).
 lbm_status make_tmaps(lbm_t h)
 {
     static EncodeTiledFn encode = nullptr;
@@ -303,6 +307,10 @@ lbm_status make_tmaps(lbm_t h)
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        const cuuint32_t sbox[3] = {(cuuint32_t)v.w, (cuuint32_t)v.h, 1};
+        r = encode(&h->tmap_st[b], dt, 3, h->pop[b], dims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
     }
     return LBM_OK;
 }

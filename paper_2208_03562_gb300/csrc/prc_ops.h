@@ -44,7 +44,10 @@ struct Variant {
     int threads;      // CTA size
     int ctas_per_sm;  // resident CTAs per SM (shared memory / register budget)
     cudaError_t (*prepare)();
-    cudaError_t (*launch)(const CUtensorMap *tsrc, const void *src, void *dst, const Plan &pl, const Grid &gd,
+    // tsrc: load descriptor of the source set (box = tile + ring); tdst:
+    // store descriptor of the destination set (box = tile)
+    cudaError_t (*launch)(const CUtensorMap *tsrc, const CUtensorMap *tdst, const void *src, void *dst, const Plan &pl,
+                          const Grid &gd,
                           const Coef<double> &k, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
                           bool force, cudaStream_t s);
 };

@@ -12,7 +12,7 @@ using S = PRC_S;
 using T = PRC_T;
 
 struct TmaArgs {
-    const CUtensorMap *tsrc;
+    const CUtensorMap *tsrc, *tdst;
     const S *a;
     S *b;
     Coef<F2> k;
@@ -27,7 +27,7 @@ cudaError_t launch_tma_t(const TmaArgs &x, const Plan &pl, const Grid &gd, cudaS
 {
     using Cf = TmaCfg<S, W, H, THREADS>;
     k_step_tma<S, W, H, THREADS, MINB, DRHO, EPI, FORCE><<<pl.n_int_ctas, THREADS, Cf::SMEM, s>>>(
-        *x.tsrc, x.a, x.b, gd, x.k, x.kf, x.sn, x.partials, x.st, pl.in, pl.edge);
+        *x.tsrc, *x.tdst, x.a, x.b, gd, x.k, x.kf, x.sn, x.partials, x.st, pl.in, pl.edge);
     return cudaGetLastError();
 }
 
@@ -39,11 +39,12 @@ cudaError_t launch_tma_f(const TmaArgs &x, const Plan &pl, const Grid &gd, bool 
 }
 
 template <int W, int H, int THREADS, int MINB>
-cudaError_t launch_tma(const CUtensorMap *tsrc, const void *src, void *dst, const Plan &pl, const Grid &gd,
+cudaError_t launch_tma(const CUtensorMap *tsrc, const CUtensorMap *tdst, const void *src, void *dst, const Plan &pl,
+                       const Grid &gd,
                        const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
                        bool force, cudaStream_t s)
 {
-    const TmaArgs x{tsrc, static_cast<const S *>(src), static_cast<S *>(dst), cast_coef<F2>(kd),
+    const TmaArgs x{tsrc, tdst, static_cast<const S *>(src), static_cast<S *>(dst), cast_coef<F2>(kd),
                     cast_coef<float>(kd), static_cast<float *>(snap), partials, st};
     if (drho) {
         if (epi) return launch_tma_f<W, H, THREADS, MINB, true, true>(x, pl, gd, force, s);

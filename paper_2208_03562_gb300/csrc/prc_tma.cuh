@@ -70,6 +70,23 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// Tiled TMA store of a box from shared memory (bulk-group completion), and
+// the bulk-group bookkeeping around it.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int c0, int c1, int c2)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed store has finished reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// make this thread's shared-memory writes visible to the async (TMA) proxy
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Interior tiling: tile (tx, ty) nominally starts at (ix0 + tx W, iy0 + ty H);
 // the last column / row of tiles is shifted back to start at xlast / ylast so
 // that the tiles end right at the interior boundary.  Nodes of a shifted tile
@@ -91,7 +108,12 @@ struct TmaCfg {
     static constexpr int STAGE_BYTES = 9 * PLANE_BYTES;
     static constexpr int RW = W + 4, RH = H + 2;      // density tile: node lx at column lx + 2
     static constexpr int R_BYTES = (RW * RH * 4 + 127) / 128 * 128;
-    static constexpr int SMEM = 2 * STAGE_BYTES + 2 * R_BYTES + 128 + 128;  // two density tiles, + barriers, + base alignment
+    // FP16 storage writes each tile through a shared output tile and TMA
+    // stores (two buffers); FP32 stores straight from registers
+    static constexpr bool TSTORE = sizeof(S) == 2;
+    static constexpr int OUT_PLANE = W * H * (int)sizeof(S);  // bytes of one plane of the output tile
+    static constexpr int OUT_BYTES = TSTORE ? 9 * OUT_PLANE : 0;
+    static constexpr int SMEM = 2 * STAGE_BYTES + 2 * R_BYTES + 2 * OUT_BYTES + 128 + 128;  // + barriers, + base alignment
     static constexpr int THREADS = THREADS_;
     static constexpr int PAIRS = W / 2;               // node pairs per tile row
     static constexpr int NQ = H * PAIRS / THREADS;    // node pairs per thread per tile
@@ -139,6 +161,15 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
 // general tile body with bounce-back and the lid, plain loads), so that one
 // launch is one time step.
 //
+// FP16 storage: the collided pairs go to a shared output tile (two buffers,
+// alternating by tile), and thread 0 writes a tile with nine tiled TMA stores
+// right after the next tile's barrier (every thread has written and fenced
+// its part by then); before a buffer is refilled, thread 0 waits until the
+// stores issued from it have read it.  This replaces nine global stores and
+// their 64-bit address arithmetic per pair with shared-memory stores at fixed
+// offsets.  FP32 storage stores from registers (its shared memory is taken by
+// the wider staging windows).
+//
 // Per tile: every thread pulls its pairs from the staged planes once and
 // keeps the nine values of each in registers; the density of the pairs (and
 // of one ring unit for the first 2 W/2 + 2 (H + 2) threads) goes to the
@@ -152,7 +183,8 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
 // every thread reaches only once its collision of this tile is done).
 template <typename S, int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(THREADS, MINB)
-k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, S *__restrict__ dst, Grid gd,
+k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUtensorMap tdst,
+           const S *__restrict__ src, S *__restrict__ dst, Grid gd,
            Coef<F2> k, Coef<float> kf, float *__restrict__ snap, double2 *__restrict__ partials,
            DevStatus *__restrict__ st, Interior in, const __grid_constant__ Rects edge)
 {
@@ -160,6 +192,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
     static_assert(C::NQ >= 1 && C::NQ * THREADS == H * C::PAIRS, "whole node pairs per thread");
     static_assert(2 * C::PAIRS + 2 * C::RH <= THREADS, "one ring unit per thread at most");
     static_assert(C::R_BYTES >= srho_floats(THREADS) * (int)sizeof(float), "density tile too small for the strips");
+    static_assert(C::OUT_PLANE % 128 == 0, "TMA store sources start on 128-byte boundaries");
     if (st->stop) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // 128-byte aligned base; offsetting the shared array (rather than casting
@@ -168,7 +201,10 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
     S *stage0 = reinterpret_cast<S *>(smem);
     S *stage1 = reinterpret_cast<S *>(smem + C::STAGE_BYTES);
     float *R = reinterpret_cast<float *>(smem + 2 * C::STAGE_BYTES);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE_BYTES + 2 * C::R_BYTES);
+    S *out0 = reinterpret_cast<S *>(smem + 2 * C::STAGE_BYTES + 2 * C::R_BYTES);
+    S *out1 = reinterpret_cast<S *>(smem + 2 * C::STAGE_BYTES + 2 * C::R_BYTES + C::OUT_BYTES);
+    constexpr int OPE = C::OUT_PLANE / (int)sizeof(S);  // elements per output-tile plane
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * C::STAGE_BYTES + 2 * C::R_BYTES + 2 * C::OUT_BYTES);
     constexpr int RF = C::R_BYTES / (int)sizeof(float);  // floats per density tile
     constexpr int PE = C::PLANE_BYTES / (int)sizeof(S);  // plane stride in elements
     constexpr int RING = 2 * C::PAIRS + 2 * C::RH;        // ring units: 2 rows of pairs, 2 columns
@@ -209,6 +245,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
     // tiles per iteration without a division
     int tcx = blockIdx.x % in.ntx, tcy = blockIdx.x / in.ntx;
     const int sdx = gridDim.x % in.ntx, sdy = gridDim.x / in.ntx;
+    int px0 = 0, py0 = 0;  // origin of the previous tile (its TMA store is issued one tile later)
     int it = 0;
     for (; tile < ntiles; it++, tile += gridDim.x) {
         const int s = it & 1;
@@ -269,6 +306,11 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                 }
             }
         }
+        if constexpr (C::TSTORE) {
+            // the store of tile it - 2 (issued one tile ago) has read its
+            // output buffer, which this tile's collision refills
+            if (tid == 0) bulk_wait_read_all();
+        }
         // every pull from `cur` is done and R[s] is complete
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -276,10 +318,23 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                 atomicExch(&st->stop, 1);
                 // the copies of the next tile into the other stage may be outstanding
                 if (tile + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
+                if constexpr (C::TSTORE) bulk_wait_all();
             }
             return;
         }
-        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, cur, &bar[s]);
+        if (tid == 0) {
+            if (tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, cur, &bar[s]);
+            if constexpr (C::TSTORE) {
+                // store the previous tile: every thread wrote and fenced its
+                // part of the output buffer before the barrier above
+                if (it > 0) {
+                    const S *o = s ? out0 : out1;
+#pragma unroll
+                    for (int i = 0; i < 9; i++) tma_store_3d(&tdst, o + i * OPE, px0, py0, i);
+                    bulk_commit();
+                }
+            }
+        }
 #pragma unroll
         for (int j = 0; j < C::NQ; j++) {
             const int ly = ly0 + j * DY;
@@ -305,8 +360,14 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
             F2 ux, uy, drho;
             collide<F2, DRHO, FORCE>(k, g[j], dxr, dyr, ux, uy, drho);
             const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
+            if constexpr (C::TSTORE) {
+                S *ob = (s ? out1 : out0) + ly * W + x;
 #pragma unroll
-            for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[j][i]);
+                for (int i = 0; i < 9; i++) Pair<S>::store(ob + i * OPE, g[j][i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * gd.plane + o, g[j][i]);
+            }
             if constexpr (EPI) {
                 if (own_x & (y0 + ly >= oy)) {
                     __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
@@ -316,8 +377,19 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
                 }
             }
         }
+        if constexpr (C::TSTORE) fence_async_shared();  // this thread's output-tile writes, before the next barrier
+        px0 = x0;
+        py0 = y0;
     }
     __syncthreads();  // every collision is done: R is free
+    if constexpr (C::TSTORE) {
+        if (tid == 0 && it > 0) {  // the last tile's store
+            const S *o = ((it - 1) & 1) ? out1 : out0;
+#pragma unroll
+            for (int i = 0; i < 9; i++) tma_store_3d(&tdst, o + i * OPE, px0, py0, i);
+            bulk_commit();
+        }
+    }
     // edge strips: general tile body, density tile in R
     for (int e = blockIdx.x; e < edge.start[edge.n]; e += gridDim.x) {
         int ex0, ey0, ex1, ey1, lw;
@@ -329,6 +401,9 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const S *__restrict__ src, 
         double a, b;
         acc.block_total(a, b, red);
         if (tid == 0) partials[blockIdx.x] = make_double2(a, b);
+    }
+    if constexpr (C::TSTORE) {
+        if (tid == 0) bulk_wait_all();  // the output tiles stay allocated until the stores are done
     }
 }
 
