@@ -159,11 +159,18 @@ TMA_CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", range(4))
 @pytest.mark.parametrize("case", TMA_CASES)
 @pytest.mark.parametrize("dtype", [L.F32, L.F16])
-def test_interior_kernel_matches_oracle(case, dtype):
+def test_interior_kernel_matches_oracle(case, dtype, variant):
+    """Each compiled shape of the interior kernel, selected explicitly (these
+    grids would otherwise run on the cluster engine); a grid too small for a
+    shape's tiles runs the general kernel under that selection."""
     nx, ny, r, gamma, nu, u_lid, bc, drho = case
     g, o = pair(nx, ny, r, gamma, nu, u_lid, dtype, bc, drho)
+    assert variant < L.lbm_variant_count(dtype)
+    g.variant = variant
+    assert g.variant == variant
     random_start(g, o, seed=nx + ny, amp=1e-3)
     w = S.rest_weights(o.p)[:, None, None]
     tol = 2e-7 if dtype == L.F32 else 2e-5
@@ -290,16 +297,27 @@ def test_fp16_then_fp32_promotion_reaches_1e6():
     assert rel_l2_u(g32.fields(), o.fields()) < 1e-3
 
 
-def test_full_size_shallow_cavity_fp32_sampled():
-    """The 8192 x 2048 workload in the launch configuration of the benchmark:
-    40 steps from rest, compared with the oracle on every node."""
+@pytest.mark.parametrize("dtype,tol", [(L.F32, 1e-5), (L.F16, 5e-3)])
+def test_full_size_shallow_cavity_sampled(dtype, tol):
+    """The 8192 x 2048 workload in the launch configurations of the benchmark
+    (every interior-kernel shape the autotuner can pick, on a workspace from
+    PyTorch): 40 steps from rest, compared with the oracle on every node.
+    FP16: stored deviations keep 11 significant bits, so the velocity near the
+    lid carries relative rounding noise of a few 1e-4 per step."""
     cav = I.shallow_cavity_8192x2048("f32")
-    g, o = pair(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.F32, torch_ws=True)
-    g.step(40)
+    o = S.Oracle(S.OracleParams(nx=cav.nx, ny=cav.ny, r=cav.r, gamma=cav.gamma, nu=cav.nu, u_lid=cav.u_lid))
     o.step(40)
-    a, b = g.fields(), o.fields()
-    assert rel_l2_u(a, b) < 1e-5
-    assert abs(g.mass() - oracle_mass(o)) < 1e-6 * cav.nodes
+    b = o.fields()
+    mo = oracle_mass(o)
+    for v in range(L.lbm_variant_count(dtype)):
+        p = L.lbm_params_init(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, dtype)
+        g = L.Lbm(p, torch_workspace=True)
+        g.variant = v
+        g.step(40)
+        a = g.fields()
+        assert rel_l2_u(a, b) < tol, (v, rel_l2_u(a, b))
+        assert abs(g.mass() - mo) < 1e-6 * cav.nodes, (v, g.mass() - mo)
+        g.close()
 
 
 @pytest.mark.parametrize("dtype,tol", [(L.F64, 1e-13), (L.F32, 1e-9), (L.F16, 1e-5)])
