@@ -48,46 +48,64 @@ __host__ __device__ inline size_t cluster_smem_bytes(int rows, int nx, size_t el
     return fa + (size_t)(rows + 2) * (nx + 2) * telem;
 }
 
-// Read access to one population set of the cluster: this CTA's slab, the
-// two neighbouring slabs (rows within two of the slab) and, across a periodic
-// wrap, any slab.
+// Load of one stored population through a 32-bit shared::cluster address
+// (this CTA's shared memory or another CTA's of the cluster), widened to the
+// collision type.  Volatile: the loads must stay between the cluster
+// barriers that order them against the neighbours' stores.
 template <typename S, typename T>
+__device__ __forceinline__ T ld_cl(uint32_t a);
+template <>
+__device__ __forceinline__ double ld_cl<double, double>(uint32_t a)
+{
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+template <>
+__device__ __forceinline__ float ld_cl<float, float>(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+template <>
+__device__ __forceinline__ float ld_cl<__half, float>(uint32_t a)
+{
+    unsigned short v;
+    asm volatile("ld.shared::cluster.b16 %0, [%1];" : "=h"(v) : "r"(a));
+    return __half2float(__ushort_as_half(v));
+}
+
+// shared::cta address of a pointer into this CTA's shared memory
+__device__ __forceinline__ uint32_t cta_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// the same location in the shared memory of CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t cta_addr, int rank)
+{
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(cta_addr), "r"(rank));
+    return a;
+}
+
+// Read access to one population set of the cluster in 32-bit shared::cluster
+// addresses: this CTA's slab, the two neighbouring slabs (rows within two of
+// the slab) and, across a periodic wrap, any slab.  Every CTA lays its set
+// out the same way: plane i, local row ly, column x at i plane_b + ly row_b +
+// x sizeof(S) from the set's base.
 struct SlabView {
-    const S *own, *prev, *next;  // the set in this CTA and in the neighbouring CTAs
-    int y_lo, y_hi, rpc, nx, nc;
-    long long plane;             // rpc * nx (same layout in every CTA)
+    uint32_t own, prev, next;  // base of the set in this CTA and in the neighbouring CTAs
+    uint32_t own_cta;          // base of the set in this CTA's shared::cta window (mapa source on a wrap)
+    int y_lo, y_hi, rpc, nc;
+    uint32_t row_b, plane_b;   // bytes per row and per plane
 
-    // plane-0 address of the in-domain row y (any slab)
-    __device__ __forceinline__ const S *row(int y) const
+    // address of plane 0, column 0 of the in-domain row y (any slab)
+    __device__ __forceinline__ uint32_t row(int y) const
     {
-        if (y >= y_lo && y < y_hi) return own + (long long)(y - y_lo) * nx;
-        if (y < y_lo && y >= y_lo - 2) return prev + (long long)(y - (y_lo - rpc)) * nx;
-        if (y >= y_hi && y < y_hi + 2) return next + (long long)(y - y_hi) * nx;
-        auto cl = cooperative_groups::this_cluster();
-        const int owner = min(y / rpc, nc - 1);
-        return cl.map_shared_rank(const_cast<S *>(own), owner) + (long long)(y - owner * rpc) * nx;
-    }
-
-    __device__ __forceinline__ T ld(int i, int x, int y) const
-    {
-        const S *base;
-        int ly;
-        if (y >= y_lo && y < y_hi) {
-            base = own;
-            ly = y - y_lo;
-        } else if (y < y_lo && y >= y_lo - 2) {
-            base = prev;
-            ly = y - (y_lo - rpc);
-        } else if (y >= y_hi && y < y_hi + 2) {
-            base = next;
-            ly = y - y_hi;
-        } else {  // periodic wrap across the first / last slab
-            auto cl = cooperative_groups::this_cluster();
-            const int owner = min(y / rpc, nc - 1);
-            base = cl.map_shared_rank(const_cast<S *>(own), owner);
-            ly = y - owner * rpc;
-        }
-        return ld_smem<S, T>(base + (long long)i * plane + (long long)ly * nx + x);
+        if (y >= y_lo && y < y_hi) return own + (uint32_t)(y - y_lo) * row_b;
+        if (y < y_lo && y >= y_lo - 2) return prev + (uint32_t)(y - (y_lo - rpc)) * row_b;
+        if (y >= y_hi && y < y_hi + 2) return next + (uint32_t)(y - y_hi) * row_b;
+        const int owner = min(y / rpc, nc - 1);  // periodic wrap across the first / last slab
+        return cluster_addr(own_cta, owner) + (uint32_t)(y - owner * rpc) * row_b;
     }
 };
 
@@ -97,18 +115,20 @@ struct SlabView {
 // fast path: the three source rows are resolved once and the nine pulls are
 // fixed offsets from them.
 template <typename S, typename T>
-__device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &gd, int x, int y, T lid, T g[9])
+__device__ __forceinline__ void pull9_slab(const SlabView &v, const Grid &gd, int x, int y, T lid, T g[9])
 {
+    constexpr uint32_t es = sizeof(S);
     const bool xin = (x >= 1) & (x <= gd.nx - 2);
     const bool yin = (gd.bc == 2) | ((y >= 1) & (y <= gd.ny - 2));
     if (xin & yin) {
         const int ym = y == 0 ? gd.ny - 1 : y - 1, yp = y == gd.ny - 1 ? 0 : y + 1;
-        const S *rr[3] = {v.row(ym), v.row(y), v.row(yp)};  // source row of e_y = +1, 0, -1
+        const uint32_t rr[3] = {v.row(ym), v.row(y), v.row(yp)};  // source row of e_y = +1, 0, -1
 #pragma unroll
         for (int i = 0; i < 9; i++)
-            g[i] = ld_smem<S, T>(rr[1 - ey_of(i)] + (long long)i * v.plane + (x - ex_of(i)));
+            g[i] = ld_cl<S, T>(rr[1 - ey_of(i)] + (uint32_t)i * v.plane_b + (uint32_t)(x - ex_of(i)) * es);
         return;
     }
+    const uint32_t here = v.row(y) + (uint32_t)x * es;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
@@ -116,9 +136,9 @@ __device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &
         if (gd.bc == 2) sy = sy < 0 ? sy + gd.ny : (sy >= gd.ny ? sy - gd.ny : sy);
         const bool inside = (sx >= 0) & (sx < gd.nx) & (sy >= 0) & (sy < gd.ny);
         if (inside) {
-            g[i] = v.ld(i, sx, sy);
+            g[i] = ld_cl<S, T>(v.row(sy) + (uint32_t)i * v.plane_b + (uint32_t)sx * es);
         } else {
-            T w = v.ld(opp_of(i), x, y);
+            T w = ld_cl<S, T>(here + (uint32_t)opp_of(i) * v.plane_b);
             if (sy >= gd.ny && gd.lid_on) {
                 if (i == 7) w -= lid;
                 if (i == 8) w += lid;
@@ -126,6 +146,32 @@ __device__ __forceinline__ void pull9_slab(const SlabView<S, T> &v, const Grid &
             g[i] = w;
         }
     }
+}
+
+// The nine pulls of the node pair (x, x + 1) in FP32, one pair of source rows
+// resolved for both nodes when all eighteen sources are inside the domain.
+template <typename S>
+__device__ __forceinline__ void pull_pair_slab(const SlabView &v, const Grid &gd, int x, int y, bool v1,
+                                               float lid, float ga[9], float gb[9])
+{
+    constexpr uint32_t es = sizeof(S);
+    const bool fast = (x >= 1) & (x + 2 <= gd.nx - 1) & ((gd.bc == 2) | ((y >= 1) & (y <= gd.ny - 2)));
+    if (fast) {
+        const int ym = y == 0 ? gd.ny - 1 : y - 1, yp = y == gd.ny - 1 ? 0 : y + 1;
+        const uint32_t rr[3] = {v.row(ym), v.row(y), v.row(yp)};
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const uint32_t a = rr[1 - ey_of(i)] + (uint32_t)i * v.plane_b + (uint32_t)(x - ex_of(i)) * es;
+            ga[i] = ld_cl<S, float>(a);
+            gb[i] = ld_cl<S, float>(a + es);
+        }
+        return;
+    }
+    pull9_slab<S, float>(v, gd, x, y, lid, ga);
+    if (v1) pull9_slab<S, float>(v, gd, x + 1, y, lid, gb);
+    else
+#pragma unroll
+        for (int i = 0; i < 9; i++) gb[i] = ga[i];
 }
 
 // n time steps of one instance on one cluster (gridDim.x == cluster size).
@@ -147,21 +193,25 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     const int nc = (int)cl.num_blocks(), rank = (int)cl.block_rank();
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int nx = gd.nx;
-    SlabView<S, T> v;
+    const int plane = rpc * nx;  // elements per plane of a slab (the same layout in every CTA)
+    SlabView v;
     v.rpc = rpc;
-    v.nx = nx;
     v.nc = nc;
     v.y_lo = rank * rpc;
     v.y_hi = min(v.y_lo + rpc, gd.ny);
-    v.plane = (long long)rpc * nx;
+    v.row_b = (uint32_t)nx * (uint32_t)sizeof(S);
+    v.plane_b = (uint32_t)plane * (uint32_t)sizeof(S);
     const int rows = v.y_hi - v.y_lo;
     const size_t fbytes = (2 * 9 * (size_t)rpc * nx * sizeof(S) + 15) / 16 * 16;
     S *F0 = reinterpret_cast<S *>(cl_smem);
-    S *F1 = F0 + 9 * v.plane;
+    S *F1 = F0 + 9 * plane;
     T *rho = reinterpret_cast<T *>(cl_smem + fbytes);
     const int prv = rank > 0 ? rank - 1 : nc - 1, nxt = rank + 1 < nc ? rank + 1 : 0;
-    const S *prev0 = cl.map_shared_rank(F0, prv), *prev1 = cl.map_shared_rank(F1, prv);
-    const S *next0 = cl.map_shared_rank(F0, nxt), *next1 = cl.map_shared_rank(F1, nxt);
+    // 32-bit shared::cluster addresses of both sets in this CTA and its neighbours
+    const uint32_t own0c = cta_smem_addr(F0), own1c = cta_smem_addr(F1);  // shared::cta window
+    const uint32_t own0 = cluster_addr(own0c, rank), own1 = cluster_addr(own1c, rank);
+    const uint32_t prev0 = cluster_addr(own0c, prv), prev1 = cluster_addr(own1c, prv);
+    const uint32_t next0 = cluster_addr(own0c, nxt), next1 = cluster_addr(own1c, nxt);
 
     // load the slab of the current state
     const S *pin = (t0 & 1) ? pop1 : pop0;
@@ -176,7 +226,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     for (int i = 0; i < 9; i++)
         for (int q = tid; q < nslab; q += nthr) {
             const int ly = q / nx, x = q - ly * nx;
-            F0[i * v.plane + (long long)ly * nx + x] =
+            F0[i * plane + ly * nx + x] =
                 pin[(long long)i * gd.plane + (long long)(v.y_lo + ly) * gd.pitch + x];
         }
     cl.sync();
@@ -187,7 +237,8 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     for (; done < nsteps; done++) {
         const long long t = t0 + done + 1;  // absolute index of the step being made
         const bool epi = (t % 20) == 0;
-        v.own = b ? F1 : F0;
+        v.own = b ? own1 : own0;
+        v.own_cta = b ? own1c : own0c;
         v.prev = b ? prev1 : prev0;
         v.next = b ? next1 : next0;
         S *Fo = b ? F0 : F1;
@@ -230,11 +281,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 const int y = v.y_lo + ly;
                 const bool v1 = x + 1 < nx;
                 float ga[9], gb[9];
-                pull9_slab<S, float>(v, gd, x, y, k.lid, ga);
-                if (v1) pull9_slab<S, float>(v, gd, x + 1, y, k.lid, gb);
-                else
-#pragma unroll
-                    for (int i = 0; i < 9; i++) gb[i] = ga[i];
+                pull_pair_slab<S>(v, gd, x, y, v1, k.lid, ga, gb);
                 F2 g[9];
 #pragma unroll
                 for (int i = 0; i < 9; i++) g[i] = F2(ga[i], gb[i]);
@@ -253,11 +300,11 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 }
                 F2 ux, uy, drho;
                 collide<F2, DRHO, FORCE, RAW>(k2, g, F2(dx[0], dx[1]), F2(dy[0], dy[1]), ux, uy, drho);
-                const long long o = (long long)ly * nx + x;
+                const int o = ly * nx + x;
 #pragma unroll
                 for (int i = 0; i < 9; i++) {
-                    Fo[i * v.plane + o] = to_s<S, float>(g[i].v.x);
-                    if (v1) Fo[i * v.plane + o + 1] = to_s<S, float>(g[i].v.y);
+                    Fo[i * plane + o] = to_s<S, float>(g[i].v.x);
+                    if (v1) Fo[i * plane + o + 1] = to_s<S, float>(g[i].v.y);
                 }
                 if (epi) {
                     const long long og = (long long)y * gd.pitch + x;
@@ -296,9 +343,9 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
             }
             T ux, uy, drho;
             collide<T, DRHO, FORCE, RAW>(k, g, dxr, dyr, ux, uy, drho);
-            const long long o = (long long)ly * nx + x;
+            const int o = ly * nx + x;
 #pragma unroll
-            for (int i = 0; i < 9; i++) Fo[i * v.plane + o] = to_s<S, T>(g[i]);
+            for (int i = 0; i < 9; i++) Fo[i * plane + o] = to_s<S, T>(g[i]);
             if (epi) {
                 const long long og = (long long)y * gd.pitch + x;
                 const T d = ux - snap[og];
@@ -351,7 +398,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
         for (int q = tid; q < nslab; q += nthr) {
             const int ly = q / nx, x = q - ly * nx;
             pout[(long long)i * gd.plane + (long long)(v.y_lo + ly) * gd.pitch + x] =
-                (b ? F1 : F0)[i * v.plane + (long long)ly * nx + x];
+                (b ? F1 : F0)[i * plane + ly * nx + x];
         }
 }
 
