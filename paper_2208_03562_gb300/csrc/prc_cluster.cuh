@@ -242,8 +242,8 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
         v.prev = b ? prev1 : prev0;
         v.next = b ? next1 : next0;
         S *Fo = b ? F0 : F1;
-        // 1. density tile (slab + ring)
-        if constexpr (DRHO) {
+        // 1. density tile (slab + ring), one node at a time
+        auto density_pass = [&]() {
             const int nr = (rows + 2) * RW;
             int ry = r_ly0, rx = r_x0;
             for (int q = tid; q < nr; q += nthr) {
@@ -261,27 +261,16 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 rho[q] = sum9(g);
             }
             __syncthreads();
-        }
-        // 2. collide every slab node into the other set
+        };
         RedAcc<T> acc;
         if constexpr (std::is_same<T, float>::value) {
             // FP32 collision: pairs of neighbouring nodes (x, x + 1), x even,
             // in packed FP32x2 arithmetic, as in the general kernel
             const int npx = (nx + 1) >> 1, npairs = rows * npx;
-            const int p_dly = nthr / npx, p_dx = nthr - p_dly * npx;
-            int py = tid / npx, pxi = tid - py * npx;
-            for (int q = tid; q < npairs; q += nthr) {
-                const int ly = py, x = 2 * pxi;
-                pxi += p_dx;
-                py += p_dly;
-                if (pxi >= npx) {
-                    pxi -= npx;
-                    py++;
-                }
+            // 2. collide one pair (pulled values in ga, gb) into the other set
+            auto pair_body = [&](int ly, int x, const float *ga, const float *gb) {
                 const int y = v.y_lo + ly;
                 const bool v1 = x + 1 < nx;
-                float ga[9], gb[9];
-                pull_pair_slab<S>(v, gd, x, y, v1, k.lid, ga, gb);
                 F2 g[9];
 #pragma unroll
                 for (int i = 0; i < 9; i++) g[i] = F2(ga[i], gb[i]);
@@ -317,42 +306,98 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                         acc.add(d1 * d1, drho.v.y);
                     }
                 }
+            };
+            if (npairs <= nthr) {
+                // one pair per thread: its pulls stay in registers across the
+                // density barrier, and the density pass only adds the ring
+                const bool act = tid < npairs;
+                const int ly = tid / npx, x = 2 * (tid - ly * npx);
+                float ga[9], gb[9];
+                if (act) pull_pair_slab<S>(v, gd, x, v.y_lo + ly, x + 1 < nx, k.lid, ga, gb);
+                if constexpr (DRHO) {
+                    if (act) {
+                        rho[(ly + 1) * RW + x + 1] = sum9(ga);
+                        if (x + 1 < nx) rho[(ly + 1) * RW + x + 2] = sum9(gb);
+                    }
+                    const int nring = 2 * RW + 2 * rows;  // rows -1 and `rows`, columns -1 and nx
+                    for (int q = tid; q < nring; q += nthr) {
+                        int lx, rl;
+                        if (q < RW) {
+                            lx = q - 1;
+                            rl = -1;
+                        } else if (q < 2 * RW) {
+                            lx = q - RW - 1;
+                            rl = rows;
+                        } else if (q < 2 * RW + rows) {
+                            lx = -1;
+                            rl = q - 2 * RW;
+                        } else {
+                            lx = nx;
+                            rl = q - 2 * RW - rows;
+                        }
+                        int gx = lx, gy = v.y_lo + rl;
+                        map_node(gd, gx, gy);
+                        float gr[9];
+                        pull9_slab<S, float>(v, gd, gx, gy, k.lid, gr);
+                        rho[(rl + 1) * RW + lx + 1] = sum9(gr);
+                    }
+                    __syncthreads();
+                }
+                if (act) pair_body(ly, x, ga, gb);
+            } else {
+                if constexpr (DRHO) density_pass();
+                const int p_dly = nthr / npx, p_dx = nthr - p_dly * npx;
+                int py = tid / npx, pxi = tid - py * npx;
+                for (int q = tid; q < npairs; q += nthr) {
+                    const int ly = py, x = 2 * pxi;
+                    pxi += p_dx;
+                    py += p_dly;
+                    if (pxi >= npx) {
+                        pxi -= npx;
+                        py++;
+                    }
+                    float ga[9], gb[9];
+                    pull_pair_slab<S>(v, gd, x, v.y_lo + ly, x + 1 < nx, k.lid, ga, gb);
+                    pair_body(ly, x, ga, gb);
+                }
             }
         } else {
-        int sy_ = s_ly0, sx_ = s_x0;
-        for (int q = tid; q < nslab; q += nthr) {
-            const int ly = sy_, x = sx_;
-            sx_ += s_dx;
-            sy_ += s_dly;
-            if (sx_ >= nx) {
-                sx_ -= nx;
-                sy_++;
-            }
-            const int y = v.y_lo + ly;
-            T g[9];
-            pull9_slab<S, T>(v, gd, x, y, k.lid, g);
-            T dxr = T(0), dyr = T(0);
-            if constexpr (DRHO) {
-                const T *c = rho + (ly + 1) * RW + x + 1;
-                const T rE = c[1], rW = c[-1];
-                const T rN = c[RW], rS = c[-RW];
-                const T rNE = c[RW + 1], rNW = c[RW - 1];
-                const T rSE = c[-RW + 1], rSW = c[-RW - 1];
-                dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
-                dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
-            }
-            T ux, uy, drho;
-            collide<T, DRHO, FORCE, RAW>(k, g, dxr, dyr, ux, uy, drho);
-            const int o = ly * nx + x;
+            // FP64 collision: one node at a time
+            if constexpr (DRHO) density_pass();
+            int sy_ = s_ly0, sx_ = s_x0;
+            for (int q = tid; q < nslab; q += nthr) {
+                const int ly = sy_, x = sx_;
+                sx_ += s_dx;
+                sy_ += s_dly;
+                if (sx_ >= nx) {
+                    sx_ -= nx;
+                    sy_++;
+                }
+                const int y = v.y_lo + ly;
+                T g[9];
+                pull9_slab<S, T>(v, gd, x, y, k.lid, g);
+                T dxr = T(0), dyr = T(0);
+                if constexpr (DRHO) {
+                    const T *c = rho + (ly + 1) * RW + x + 1;
+                    const T rE = c[1], rW = c[-1];
+                    const T rN = c[RW], rS = c[-RW];
+                    const T rNE = c[RW + 1], rNW = c[RW - 1];
+                    const T rSE = c[-RW + 1], rSW = c[-RW - 1];
+                    dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
+                    dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+                }
+                T ux, uy, drho;
+                collide<T, DRHO, FORCE, RAW>(k, g, dxr, dyr, ux, uy, drho);
+                const int o = ly * nx + x;
 #pragma unroll
-            for (int i = 0; i < 9; i++) Fo[i * plane + o] = to_s<S, T>(g[i]);
-            if (epi) {
-                const long long og = (long long)y * gd.pitch + x;
-                const T d = ux - snap[og];
-                snap[og] = ux;
-                acc.add(d * d, drho);
+                for (int i = 0; i < 9; i++) Fo[i * plane + o] = to_s<S, T>(g[i]);
+                if (epi) {
+                    const long long og = (long long)y * gd.pitch + x;
+                    const T d = ux - snap[og];
+                    snap[og] = ux;
+                    acc.add(d * d, drho);
+                }
             }
-        }
         }
         if (epi) {
             double a, bb;
