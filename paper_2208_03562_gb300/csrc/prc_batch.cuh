@@ -131,19 +131,27 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl)
     return ok != 0;
 }
 
+// Shared memory of k_batch: the density tile of a tile (+ ring), declared once
+// for every instantiation of the tile body.
+template <typename S, typename T>
+__host__ __device__ constexpr int batch_smem_bytes()
+{
+    return std::is_same<T, float>::value ? PAIR_SRHO * 4 : srho_floats(BX * BY) * (int)sizeof(T);
+}
+
 template <typename S, typename T, bool DRHO, bool EPI, bool FORCE, bool RAW>
 __device__ __forceinline__ void batch_tile_t(const BatchInst &I, const BatchCoef<T> &k, int parity, int lt,
-                                             double2 *partials)
+                                             double2 *partials, unsigned char *bsm)
 {
     RedAcc<T> acc;
     if constexpr (std::is_same<T, float>::value) {
-        __shared__ __align__(16) float srho[PAIR_SRHO];
+        float *srho = reinterpret_cast<float *>(bsm);
         const int x0 = (lt % I.tiles_x) * PTW, y0 = (lt / I.tiles_x) * PTH;
         pair_tile<S, DRHO, EPI, FORCE, true, RAW>(static_cast<const S *>(I.pop[parity]),
                                                  static_cast<S *>(I.pop[parity ^ 1]), I.gd, k.k, k.k2,
                                                  static_cast<float *>(I.snap), x0, y0, acc, srho);
     } else {
-        __shared__ T srho[srho_floats(BX * BY)];
+        T *srho = reinterpret_cast<T *>(bsm);
         const int x0 = (lt % I.tiles_x) * BX, y0 = (lt / I.tiles_x) * BY;
         general_tile<S, T, DRHO, EPI, FORCE, true, RAW>(static_cast<const S *>(I.pop[parity]),
                                                    static_cast<S *>(I.pop[parity ^ 1]), I.gd, k.k,
@@ -161,33 +169,33 @@ __device__ __forceinline__ void batch_tile_t(const BatchInst &I, const BatchCoef
 
 template <typename S, typename T, bool RAW>
 __device__ __forceinline__ void batch_tile_m(const BatchInst &I, const BatchCoef<T> &k, int parity, int lt, bool epi,
-                                             double2 *partials)
+                                             double2 *partials, unsigned char *bsm)
 {
     if (I.drho) {
         if (I.force) {
-            if (epi) batch_tile_t<S, T, true, true, true, RAW>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, true, false, true, RAW>(I, k, parity, lt, partials);
+            if (epi) batch_tile_t<S, T, true, true, true, RAW>(I, k, parity, lt, partials, bsm);
+            else batch_tile_t<S, T, true, false, true, RAW>(I, k, parity, lt, partials, bsm);
         } else {
-            if (epi) batch_tile_t<S, T, true, true, false, RAW>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, true, false, false, RAW>(I, k, parity, lt, partials);
+            if (epi) batch_tile_t<S, T, true, true, false, RAW>(I, k, parity, lt, partials, bsm);
+            else batch_tile_t<S, T, true, false, false, RAW>(I, k, parity, lt, partials, bsm);
         }
     } else {
         if (I.force) {
-            if (epi) batch_tile_t<S, T, false, true, true, RAW>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, false, false, true, RAW>(I, k, parity, lt, partials);
+            if (epi) batch_tile_t<S, T, false, true, true, RAW>(I, k, parity, lt, partials, bsm);
+            else batch_tile_t<S, T, false, false, true, RAW>(I, k, parity, lt, partials, bsm);
         } else {
-            if (epi) batch_tile_t<S, T, false, true, false, RAW>(I, k, parity, lt, partials);
-            else batch_tile_t<S, T, false, false, false, RAW>(I, k, parity, lt, partials);
+            if (epi) batch_tile_t<S, T, false, true, false, RAW>(I, k, parity, lt, partials, bsm);
+            else batch_tile_t<S, T, false, false, false, RAW>(I, k, parity, lt, partials, bsm);
         }
     }
 }
 
 template <typename S, typename T>
 __device__ __forceinline__ void batch_tile(const BatchInst &I, const BatchCoef<T> &k, int parity, int lt, bool epi,
-                                           double2 *partials)
+                                           double2 *partials, unsigned char *bsm)
 {
-    if (I.gd.model == 1) batch_tile_m<S, T, true>(I, k, parity, lt, epi, partials);
-    else batch_tile_m<S, T, false>(I, k, parity, lt, epi, partials);
+    if (I.gd.model == 1) batch_tile_m<S, T, true>(I, k, parity, lt, epi, partials, bsm);
+    else batch_tile_m<S, T, false>(I, k, parity, lt, epi, partials, bsm);
 }
 
 template <typename S, typename T>
@@ -196,6 +204,7 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
         int total_tiles, double2 *partials, BatchCtl *ctl, int steps)
 {
     const int tid = threadIdx.y * BX + threadIdx.x;
+    __shared__ __align__(16) unsigned char bsm[batch_smem_bytes<S, T>()];
     for (int s = 0; s < steps; s++) {
         // ---- one time step of every active instance
         int i = 0;
@@ -206,7 +215,7 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
             if (ld_relaxed_i32(&D->state) != BATCH_ACTIVE) continue;
             const long long t = __ldcg(&D->t);
             const bool epi = ((t + 1) % 20) == 0;
-            batch_tile<S, T>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start, epi, partials);
+            batch_tile<S, T>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start, epi, partials, bsm);
         }
         if (!grid_barrier(ctl)) return;
         // ---- bookkeeping: counters, residuals, retirement (one CTA per instance).

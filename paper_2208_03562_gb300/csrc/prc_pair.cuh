@@ -48,6 +48,36 @@ struct PairG<__half> {
     }
 };
 
+// map_node for the tile's nodes and its ring (at most one node before the
+// grid, any number after it in a partial tile): a conditional wrap instead of
+// a remainder.  Coordinates within one grid length of the grid map exactly as
+// in map_node; farther ones (nodes of a partial tile that no stored node
+// uses) are clamped into the grid.
+__device__ __forceinline__ void map_node_near(const Grid &gd, int &x, int &y)
+{
+    if (gd.bc >= 1) x = x < 0 ? x + gd.nx : (x >= gd.nx ? x - gd.nx : x);
+    x = min(max(x, 0), gd.nx - 1);
+    if (gd.bc == 2) y = y < 0 ? y + gd.ny : (y >= gd.ny ? y - gd.ny : y);
+    y = min(max(y, 0), gd.ny - 1);
+}
+
+// The nine pulls of node (x, y) of the grid: fixed offsets from the node when
+// every source lies inside the grid (no wall, no periodic seam), else pull9
+// with the walls and the lid.  Either way the same values as pull9.
+template <typename S, bool CG>
+__device__ __forceinline__ void pull9_any(const S *__restrict__ src, const Grid &gd, int x, int y, float lid,
+                                          float g[9])
+{
+    if ((x >= 1) & (x <= gd.nx - 2) & (y >= 1) & (y <= gd.ny - 2)) {
+        const S *c = src + (long long)y * gd.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            g[i] = ld_pop<CG, S, float>(c + (long long)i * gd.plane - (long long)ey_of(i) * gd.pitch - ex_of(i));
+    } else {
+        pull9<S, float, CG>(src, gd, x, y, lid, g);
+    }
+}
+
 // One fused time step on the 64 x 8 tile at (x0, y0) (x0 a multiple of 64);
 // all 256 threads of the CTA call it.  srho holds PAIR_SRHO floats.
 template <typename S, bool DRHO, bool EPI, bool FORCE, bool CG, bool RAW>
@@ -79,12 +109,12 @@ __device__ __forceinline__ void pair_tile(const S *__restrict__ src, S *__restri
         // per node, at the node that stands in for it outside the grid
         float ga[9], gb[9];
         int mx = xa, my = y;
-        map_node(gd, mx, my);
-        pull9<S, float, CG>(src, gd, mx, my, kf.lid, ga);
+        map_node_near(gd, mx, my);
+        pull9_any<S, CG>(src, gd, mx, my, kf.lid, ga);
         mx = xa + 1;
         my = y;
-        map_node(gd, mx, my);
-        pull9<S, float, CG>(src, gd, mx, my, kf.lid, gb);
+        map_node_near(gd, mx, my);
+        pull9_any<S, CG>(src, gd, mx, my, kf.lid, gb);
 #pragma unroll
         for (int i = 0; i < 9; i++) g[i] = F2(ga[i], gb[i]);
     }
@@ -101,9 +131,9 @@ __device__ __forceinline__ void pair_tile(const S *__restrict__ src, S *__restri
             else if (tid < 2 * (PTW + 2) + PTH) { lx = -1; ly = tid - 2 * (PTW + 2); }
             else { lx = PTW; ly = tid - 2 * (PTW + 2) - PTH; }
             int gx = x0 + lx, gy = y0 + ly;
-            map_node(gd, gx, gy);
+            map_node_near(gd, gx, gy);
             float gr[9];
-            pull9<S, float, CG>(src, gd, gx, gy, kf.lid, gr);
+            pull9_any<S, CG>(src, gd, gx, gy, kf.lid, gr);
             srho[(ly + 1) * RW + lx + 2] = sum9(gr);
         }
         __syncthreads();
@@ -151,7 +181,7 @@ __device__ __forceinline__ void pair_tile(const S *__restrict__ src, S *__restri
 // one 64 x 8 tile per CTA over the single rectangle of `rc`; the CTA totals
 // of a residual step go to partials[part0 + blockIdx.x].
 template <typename S, bool DRHO, bool EPI, bool FORCE, bool RAW>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_step_pair(const S *__restrict__ src, S *__restrict__ dst, Grid gd, Coef<float> kf, Coef<F2> k2,
             float *__restrict__ snap, double2 *__restrict__ partials, const DevStatus *__restrict__ st,
             const __grid_constant__ Rects rc, int part0)
