@@ -319,6 +319,11 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         tiles += I.tiles;
     }
     if (n == 0) return LBM_OK;  // nothing to do
+    int spec = 1;  // every active slot: density-gradient terms, no force, central moments
+    for (int q = 0; q < n; q++) {
+        const BatchInst &I = b->h_inst[q];
+        if (!I.drho || I.force || I.gd.model != LBM_MODEL_PRC) spec = 0;
+    }
     if ((size_t)tiles > b->part_cap) {
         if (b->d_partials) BCK(b, cudaFreeAsync(b->d_partials, b->stream));
         b->d_partials = nullptr;
@@ -343,7 +348,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t el = b->ops->batch_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials, b->d_ctl,
-                                                  st, grid, cs);
+                                                  st, grid, spec, cs);
             e = cudaStreamEndCapture(cs, &g);
             if (el != cudaSuccess) e = el;
         }
@@ -363,7 +368,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         BCK(b, cudaGraphLaunch(b->gexec, b->stream));
     } else {
         BCK(b, b->ops->batch_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials, b->d_ctl, st, grid,
-                                    b->stream));
+                                    spec, b->stream));
     }
     b->in_flight = true;
     return LBM_OK;

@@ -198,7 +198,10 @@ __device__ __forceinline__ void batch_tile(const BatchInst &I, const BatchCoef<T
     else batch_tile_m<S, T, false>(I, k, parity, lt, epi, partials, bsm);
 }
 
-template <typename S, typename T>
+// SPEC = 1: every instance of the launch has the density-gradient terms on,
+// no body force and the central-moment scheme, so the tile body is chosen at
+// compile time (a smaller kernel); SPEC = 0 dispatches per instance.
+template <typename S, typename T, int SPEC>
 __global__ void __launch_bounds__(BX * BY, 3)
 k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coefs, BatchDyn *dyn, int ninst,
         int total_tiles, double2 *partials, BatchCtl *ctl, int steps)
@@ -208,14 +211,28 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
     for (int s = 0; s < steps; s++) {
         // ---- one time step of every active instance
         int i = 0;
+        int ci = -1;         // instance whose state and counter were read last (they change only between steps)
+        bool active = false;
+        long long t = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             while (i + 1 < ninst && tile >= inst[i + 1].tile_start) i++;  // tiles are in instance order
             const BatchInst &I = inst[i];
-            BatchDyn *D = dyn + I.slot;
-            if (ld_relaxed_i32(&D->state) != BATCH_ACTIVE) continue;
-            const long long t = __ldcg(&D->t);
+            if (i != ci) {
+                ci = i;
+                const BatchDyn *D = dyn + I.slot;
+                active = ld_relaxed_i32(&D->state) == BATCH_ACTIVE;
+                t = __ldcg(&D->t);
+            }
+            if (!active) continue;
             const bool epi = ((t + 1) % 20) == 0;
-            batch_tile<S, T>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start, epi, partials, bsm);
+            if constexpr (SPEC == 1) {
+                if (epi) batch_tile_t<S, T, true, true, false, false>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start,
+                                                                   partials, bsm);
+                else batch_tile_t<S, T, true, false, false, false>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start,
+                                                                  partials, bsm);
+            } else {
+                batch_tile<S, T>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start, epi, partials, bsm);
+            }
         }
         if (!grid_barrier(ctl)) return;
         // ---- bookkeeping: counters, residuals, retirement (one CTA per instance).

@@ -66,8 +66,10 @@ struct DtypeOps {
     size_t coef_bytes;
     void (*coef_convert)(const Coef<double> &in, void *out);
     cudaError_t (*batch_occupancy)(int *blocks_per_sm);
+    // spec != 0: every instance has the density-gradient terms, no force and
+    // the central-moment scheme (the specialised kernel)
     cudaError_t (*batch_launch)(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int total_tiles,
-                                double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s);
+                                double2 *partials, BatchCtl *ctl, int steps, int grid, int spec, cudaStream_t s);
     cudaError_t (*init_fields)(void *dst, const Grid &gd, const Coef<double> &k, double gamma, const double *rho,
                                const double *ux, const double *uy, void *snap, cudaStream_t s);
     cudaError_t (*fields)(const void *src, const Grid &gd, const Coef<double> &k, double *rho, double *ux,

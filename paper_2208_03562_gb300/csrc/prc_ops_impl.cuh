@@ -132,19 +132,26 @@ void op_coef_convert(const Coef<double> &in, void *out)
     c->k2 = cast_coef<F2>(in);
 }
 
+// resident CTAs per SM of both forms of the batch kernel (the smaller)
 cudaError_t op_batch_occupancy(int *blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<S, T>, BX * BY, 0);
+    int a = 0, c = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch<S, T, 0>, BX * BY, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_batch<S, T, 1>, BX * BY, 0);
+    *blocks_per_sm = a < c ? a : c;
+    return e;
 }
 
 // one cooperative launch (all CTAs co-resident, as the grid barrier needs)
 cudaError_t op_batch_launch(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int total_tiles,
-                            double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s)
+                            double2 *partials, BatchCtl *ctl, int steps, int grid, int spec, cudaStream_t s)
 {
     const BatchCoef<T> *cf = static_cast<const BatchCoef<T> *>(coefs);
     void *args[] = {(void *)&inst, (void *)&cf, (void *)&dyn, (void *)&ninst, (void *)&total_tiles,
                     (void *)&partials, (void *)&ctl, (void *)&steps};
-    return cudaLaunchCooperativeKernel((const void *)k_batch<S, T>, dim3(grid), dim3(BX, BY), args, 0, s);
+    const void *k = spec ? (const void *)k_batch<S, T, 1> : (const void *)k_batch<S, T, 0>;
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(BX, BY), args, 0, s);
 }
 
 dim3 row_grid(const Grid &gd) { return dim3((gd.nx + 127) / 128, gd.ny, 1); }
