@@ -231,6 +231,58 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
         }
     cl.sync();
 
+    // One pair per thread (FP32 collision, slabs of at most `nthr` pairs):
+    // this thread's pair and its ring node are the same every step, so the
+    // addresses of their source rows in both sets are resolved once here and
+    // the per-step pulls are fixed offsets from them.
+    constexpr uint32_t es = sizeof(S);
+    const int npx1 = (nx + 1) >> 1;
+    const int p_ly = tid / npx1, p_x = 2 * (tid - p_ly * npx1), p_y = v.y_lo + p_ly;
+    const bool p_fast = (tid < rows * npx1) & (p_x >= 1) & (p_x + 2 <= nx - 1) &
+                        ((gd.bc == 2) | ((p_y >= 1) & (p_y <= gd.ny - 2)));
+    const int nring1 = 2 * RW + 2 * rows;  // density-tile ring: rows -1 and `rows`, columns -1 and nx
+    int r_lx = 0, r_rl = 0, r_gx = 0, r_gy = 0;
+    if (tid < nring1) {
+        if (tid < RW) {
+            r_lx = tid - 1;
+            r_rl = -1;
+        } else if (tid < 2 * RW) {
+            r_lx = tid - RW - 1;
+            r_rl = rows;
+        } else if (tid < 2 * RW + rows) {
+            r_lx = -1;
+            r_rl = tid - 2 * RW;
+        } else {
+            r_lx = nx;
+            r_rl = tid - 2 * RW - rows;
+        }
+        r_gx = r_lx;
+        r_gy = v.y_lo + r_rl;
+        map_node(gd, r_gx, r_gy);
+    }
+    const bool r_fast = (tid < nring1) & (r_gx >= 1) & (r_gx <= nx - 2) &
+                        ((gd.bc == 2) | ((r_gy >= 1) & (r_gy <= gd.ny - 2)));
+    uint32_t pr0[3] = {0, 0, 0}, pr1[3] = {0, 0, 0}, rr0[3] = {0, 0, 0}, rr1[3] = {0, 0, 0};
+    for (int sb = 0; sb < 2; sb++) {
+        v.own = sb ? own1 : own0;
+        v.own_cta = sb ? own1c : own0c;
+        v.prev = sb ? prev1 : prev0;
+        v.next = sb ? next1 : next0;
+        uint32_t *pr = sb ? pr1 : pr0, *rr = sb ? rr1 : rr0;
+        if (p_fast) {
+            const int ym = p_y == 0 ? gd.ny - 1 : p_y - 1, yp = p_y == gd.ny - 1 ? 0 : p_y + 1;
+            pr[0] = v.row(ym) + (uint32_t)p_x * es;  // source row of e_y = +1, 0, -1, at column p_x
+            pr[1] = v.row(p_y) + (uint32_t)p_x * es;
+            pr[2] = v.row(yp) + (uint32_t)p_x * es;
+        }
+        if (r_fast) {
+            const int ym = r_gy == 0 ? gd.ny - 1 : r_gy - 1, yp = r_gy == gd.ny - 1 ? 0 : r_gy + 1;
+            rr[0] = v.row(ym) + (uint32_t)r_gx * es;
+            rr[1] = v.row(r_gy) + (uint32_t)r_gx * es;
+            rr[2] = v.row(yp) + (uint32_t)r_gx * es;
+        }
+    }
+
     int b = 0;  // set holding the state
     int done = 0;
     const double nnodes = (double)gd.nx * (double)gd.ny;
@@ -311,16 +363,36 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 // one pair per thread: its pulls stay in registers across the
                 // density barrier, and the density pass only adds the ring
                 const bool act = tid < npairs;
-                const int ly = tid / npx, x = 2 * (tid - ly * npx);
+                const int ly = p_ly, x = p_x;
                 float ga[9], gb[9];
-                if (act) pull_pair_slab<S>(v, gd, x, v.y_lo + ly, x + 1 < nx, k.lid, ga, gb);
+                if (p_fast) {
+                    const uint32_t r0 = b ? pr1[0] : pr0[0], r1 = b ? pr1[1] : pr0[1], r2 = b ? pr1[2] : pr0[2];
+#pragma unroll
+                    for (int i = 0; i < 9; i++) {
+                        const uint32_t a = (ey_of(i) == 1 ? r0 : (ey_of(i) == 0 ? r1 : r2)) + (uint32_t)i * v.plane_b -
+                                           (uint32_t)(ex_of(i) * (int)es);
+                        ga[i] = ld_cl<S, float>(a);
+                        gb[i] = ld_cl<S, float>(a + es);
+                    }
+                } else if (act) {
+                    pull_pair_slab<S>(v, gd, x, v.y_lo + ly, x + 1 < nx, k.lid, ga, gb);
+                }
                 if constexpr (DRHO) {
                     if (act) {
                         rho[(ly + 1) * RW + x + 1] = sum9(ga);
                         if (x + 1 < nx) rho[(ly + 1) * RW + x + 2] = sum9(gb);
                     }
-                    const int nring = 2 * RW + 2 * rows;  // rows -1 and `rows`, columns -1 and nx
-                    for (int q = tid; q < nring; q += nthr) {
+                    if (r_fast) {  // this thread's ring node, sources inside the domain
+                        const uint32_t r0 = b ? rr1[0] : rr0[0], r1 = b ? rr1[1] : rr0[1], r2 = b ? rr1[2] : rr0[2];
+                        float gr[9];
+#pragma unroll
+                        for (int i = 0; i < 9; i++)
+                            gr[i] = ld_cl<S, float>((ey_of(i) == 1 ? r0 : (ey_of(i) == 0 ? r1 : r2)) +
+                                                    (uint32_t)i * v.plane_b - (uint32_t)(ex_of(i) * (int)es));
+                        rho[(r_rl + 1) * RW + r_lx + 1] = sum9(gr);
+                    }
+                    const int nring = nring1;
+                    for (int q = r_fast ? tid + nthr : tid; q < nring; q += nthr) {
                         int lx, rl;
                         if (q < RW) {
                             lx = q - 1;
