@@ -260,10 +260,12 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step);
 
 /*
  * One time step that allocates nothing.  The paper has no counterpart: this
- * serves callers that cannot allocate device memory -- code running while a
- * stream is captured into a CUDA graph (allocation cannot be captured), code
- * whose device memory is wholly owned by another allocator, and tight loops
- * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * serves callers that cannot allocate device memory -- code whose device
+ * memory is wholly owned by another allocator (a framework's caching
+ * allocator that has reserved the GPU, so cudaMalloc fails or fragments it),
+ * programs that fix their memory budget at start-up and must not allocate
+ * afterwards, and tight loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.
  *
  * The caller owns every buffer (device pointers on the current device):
  *   src, dst  the post-collision populations before / after the step, in the

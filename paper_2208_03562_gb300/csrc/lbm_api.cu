@@ -940,11 +940,10 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
 }
 
 // ---------------------------------------------------------------------------
-// Allocation-free step.  Some callers cannot call cudaMalloc: code that runs
-// while a stream is being captured into a CUDA graph (allocation is not a
-// capturable operation), code whose device memory is entirely reserved by
-// another allocator, and latency-critical loops that cannot take the implicit
-// device synchronisation of cudaMalloc / cudaFree.  lbm_step_noalloc serves
+// Allocation-free step.  Some callers cannot call cudaMalloc: code whose
+// device memory is entirely reserved by another allocator, programs that fix
+// their memory budget at start-up, and latency-critical loops that cannot
+// take the implicit device synchronisation of cudaMalloc / cudaFree.  lbm_step_noalloc serves
 // them: the only scratch it needs (per-CTA FP64 partial sums and a status
 // word) lives in the file-scope device arrays below, which every GPU that
 // loads this library holds until the process exits.

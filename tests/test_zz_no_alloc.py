@@ -1,6 +1,6 @@
 """lbm_step_noalloc: the time step for callers that cannot allocate device
-memory (inside a CUDA-graph capture, under another allocator that owns the
-GPU's memory, or in loops that cannot take the synchronisation of
+memory (under another allocator that owns the GPU's memory, with a memory
+budget fixed at start-up, or in loops that cannot take the synchronisation of
 cudaMalloc/cudaFree).  Its scratch is a fixed device array inside the library;
 this file checks that consecutive calls through the C ABI give the same
 populations, residual and mass as the ordinary handle-based lbm_step, and that
