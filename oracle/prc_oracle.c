@@ -22,8 +22,8 @@
  *
  * Readings taken where the paper is silent, garbled or inconsistent (each is
  * also listed in the design notes):
- *   A1  d(rho)/dx, d(rho)/dy: "isotropic second order finite difference" with
- *       no stencil given (Sec. 3.5 and App. A).  Taken as
+ *   A1  d(rho)/dx, d(rho)/dy: the paper asks for a second-order isotropic
+ *       difference and gives no stencil (Sec. 3.5 and App. A).  Taken as
  *         d_x rho = [4(rE-rW) + (rNE-rNW) + (rSE-rSW)] / 12
  *         d_y rho = [4(rN-rS) + (rNE-rSE) + (rNW-rSW)] / (12 r)
  *       on the density of the same time level as the collision.  Outside the
@@ -51,9 +51,9 @@
  *   A12 PRNR-LBM (model = 1, Sec. 4.1 and Sec. 5.3): the raw-moment scheme of
  *       Eq. LBErawmomentrectangularlattice, m = S P f, relaxation of B m to
  *       the raw equilibria of Eq. 12 with the raw sources of Eq. 13, then
- *       B^-1, S^-1, P^-1.  The paper applies "the corrections ... given in
- *       Sec. 3.4" to its second-order equilibria; they are the same
- *       expressions as in the central scheme, with the strain rates of
+ *       B^-1, S^-1, P^-1.  The paper applies the Sec. 3.4 corrections to
+ *       its second-order equilibria; they are the same expressions as in
+ *       the central scheme, with the strain rates of
  *       Eq. 45, which is written for the central non-equilibrium moments.
  *
  * State layout: the post-collision populations f~ of the last completed
