@@ -177,7 +177,9 @@ __device__ __forceinline__ void pull_pair_slab(const SlabView &v, const Grid &gd
 // n time steps of one instance on one cluster (gridDim.x == cluster size).
 // pop_in holds the state after step t0; the state after the last step done
 // goes to pop_out[parity of that step].
-template <typename S, typename T, bool DRHO, bool FORCE, bool RAW>
+// ONE (FP32 collision only): every slab holds at most one node pair per
+// thread, and only that path is compiled into the kernel.
+template <typename S, typename T, bool DRHO, bool FORCE, bool RAW, bool ONE>
 __global__ void __launch_bounds__(CL_THREADS, 1)
 k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<T> k, Coef<F2> k2,
           T *__restrict__ snap, DevStatus *__restrict__ st, long long t0, int nsteps, int rpc)
@@ -263,6 +265,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     const bool r_fast = (tid < nring1) & (r_gx >= 1) & (r_gx <= nx - 2) &
                         ((gd.bc == 2) | ((r_gy >= 1) & (r_gy <= gd.ny - 2)));
     uint32_t pr0[3] = {0, 0, 0}, pr1[3] = {0, 0, 0}, rr0[3] = {0, 0, 0}, rr1[3] = {0, 0, 0};
+    if constexpr (ONE)
     for (int sb = 0; sb < 2; sb++) {
         v.own = sb ? own1 : own0;
         v.own_cta = sb ? own1c : own0c;
@@ -359,7 +362,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                     }
                 }
             };
-            if (npairs <= nthr) {
+            if constexpr (ONE) {
                 // one pair per thread: its pulls stay in registers across the
                 // density barrier, and the density pass only adds the ring
                 const bool act = tid < npairs;

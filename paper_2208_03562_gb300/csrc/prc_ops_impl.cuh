@@ -213,15 +213,30 @@ cudaError_t cluster_cfg_launch(const S *p0, const S *p1, const Grid &gd, const C
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE, RAW>, p0, p1, gd, k, k2, snap, st, t0, n, rpc);
+    const bool one = std::is_same<T, float>::value && rpc * ((gd.nx + 1) / 2) <= CL_THREADS;
+    if constexpr (std::is_same<T, float>::value) {
+        if (one)
+            return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE, RAW, true>, p0, p1, gd, k, k2, snap, st, t0,
+                                      n, rpc);
+    }
+    return cudaLaunchKernelEx(&cfg, k_cluster<S, T, DRHO, FORCE, RAW, false>, p0, p1, gd, k, k2, snap, st, t0, n, rpc);
+}
+
+cudaError_t cluster_attr_one(const void *kern, int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <bool DRHO, bool FORCE, bool RAW>
 cudaError_t cluster_attr(int smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE, RAW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cluster_attr_one((const void *)k_cluster<S, T, DRHO, FORCE, RAW, false>, smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_cluster<S, T, DRHO, FORCE, RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (std::is_same<T, float>::value)
+        e = cluster_attr_one((const void *)k_cluster<S, T, DRHO, FORCE, RAW, true>, smem);
+    return e;
 }
 
 template <bool RAW>
@@ -254,7 +269,7 @@ cudaError_t op_cluster_max_active(int nc, int smem, int *n)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(n, (void *)k_cluster<S, T, true, false, false>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, (void *)k_cluster<S, T, true, false, false, false>, &cfg);
 }
 
 cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd, const Coef<double> &kd, void *snap,
