@@ -76,6 +76,12 @@ __device__ __forceinline__ float ld_cl<__half, float>(uint32_t a)
     return __half2float(__ushort_as_half(v));
 }
 
+// The two halves of a cluster barrier: arrive (releasing this thread's
+// earlier writes) and wait for every CTA's arrival (acquiring theirs).  Work
+// that needs none of the other CTAs' data can run between them.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // shared::cta address of a pointer into this CTA's shared memory
 __device__ __forceinline__ uint32_t cta_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -231,7 +237,8 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
             F0[i * plane + ly * nx + x] =
                 pin[(long long)i * gd.plane + (long long)(v.y_lo + ly) * gd.pitch + x];
         }
-    cl.sync();
+    __syncthreads();
+    cluster_arrive();  // matched by the wait at the top of the first step
 
     // One pair per thread (FP32 collision, slabs of at most `nthr` pairs):
     // this thread's pair and its ring node are the same every step, so the
@@ -288,6 +295,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
 
     int b = 0;  // set holding the state
     int done = 0;
+    bool waited = false;  // the last cluster barrier phase has been waited on
     const double nnodes = (double)gd.nx * (double)gd.ny;
     for (; done < nsteps; done++) {
         const long long t = t0 + done + 1;  // absolute index of the step being made
@@ -368,7 +376,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 const bool act = tid < npairs;
                 const int ly = p_ly, x = p_x;
                 float ga[9], gb[9];
-                if (p_fast) {
+                auto fast_pulls = [&]() {
                     const uint32_t r0 = b ? pr1[0] : pr0[0], r1 = b ? pr1[1] : pr0[1], r2 = b ? pr1[2] : pr0[2];
 #pragma unroll
                     for (int i = 0; i < 9; i++) {
@@ -377,6 +385,15 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                         ga[i] = ld_cl<S, float>(a);
                         gb[i] = ld_cl<S, float>(a + es);
                     }
+                };
+                // a pair whose source rows all lie in this CTA's slab pulls
+                // before waiting for the other CTAs of the previous step
+                const bool early = p_fast & (ly >= 1) & (ly <= rows - 2);
+                if (early) fast_pulls();
+                cluster_wait();
+                if (early) {
+                } else if (p_fast) {
+                    fast_pulls();
                 } else if (act) {
                     pull_pair_slab<S>(v, gd, x, v.y_lo + ly, x + 1 < nx, k.lid, ga, gb);
                 }
@@ -420,6 +437,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                 }
                 if (act) pair_body(ly, x, ga, gb);
             } else {
+                cluster_wait();
                 if constexpr (DRHO) density_pass();
                 const int p_dly = nthr / npx, p_dx = nthr - p_dly * npx;
                 int py = tid / npx, pxi = tid - py * npx;
@@ -438,6 +456,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
             }
         } else {
             // FP64 collision: one node at a time
+            cluster_wait();
             if constexpr (DRHO) density_pass();
             int sy_ = s_ly0, sx_ = s_x0;
             for (int q = tid; q < nslab; q += nthr) {
@@ -479,10 +498,14 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
             acc.block_total(a, bb, red);
             if (tid == 0) part = make_double2(a, bb);
         }
-        // 3. the new set is complete (and every pull of the old one done)
-        cl.sync();
+        // 3. the new set is complete (and every pull of the old one done):
+        // this CTA's stores are visible to its own threads, then it arrives;
+        // the next step waits for the others
+        __syncthreads();
+        cluster_arrive();
         b ^= 1;
         if (epi) {
+            cluster_wait();  // every CTA's partial sums are written
             if (tid == 0) {
                 double a = 0.0, m = 0.0;
                 for (int r = 0; r < nc; r++) {  // rank order: the same sums in every CTA
@@ -504,13 +527,16 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                     if (stop) st->stop = 1;
                 }
             }
-            cl.sync();  // every CTA has read the partials before they may change
-            if (sh_stop) {
+            __syncthreads();  // sh_stop is visible to every thread
+            if (sh_stop) {  // the same decision in every CTA
                 done++;
+                waited = true;
                 break;
             }
+            cluster_arrive();  // matched by the wait at the top of the next step
         }
     }
+    if (!waited) cluster_wait();  // every CTA is done with this CTA's shared memory
     // write the slab of the final state
     const long long tend = t0 + done;
     S *pout = const_cast<S *>((tend & 1) ? pop1 : pop0);
