@@ -181,8 +181,7 @@ lbm_status launch_one(lbm_t h, cudaStream_t s, long long t_before)
     const bool drho = h->p.drho == LBM_DRHO_CURRENT, force = h->p.fx != 0.0 || h->p.fy != 0.0;
     if (h->plan.tma)
         CK(h, h->ops->variants[h->variant].launch(&h->tmap[c], &h->tmap_st[c ^ 1], h->pop[c], h->pop[c ^ 1], h->plan,
-                                                   h->gd, h->k,
-                                                   h->snap, h->partials, h->st, drho, epi, force, s));
+                                                   h->gd, h->k, h->snap, h->partials, h->st, drho, epi, force, c, s));
     if (h->plan.n_edge_ctas > 0)
         CK(h, h->ops->step_general(h->pop[c], h->pop[c ^ 1], h->plan, h->gd, h->k, h->snap, h->partials, h->st,
                                    drho, epi, force, s));

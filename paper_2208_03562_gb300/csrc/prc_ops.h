@@ -46,10 +46,10 @@ struct Variant {
     cudaError_t (*prepare)();
     // tsrc: load descriptor of the source set (box = tile + ring); tdst:
     // store descriptor of the destination set (box = tile)
+    // rev: take the interior tiles in reverse order (alternate steps)
     cudaError_t (*launch)(const CUtensorMap *tsrc, const CUtensorMap *tdst, const void *src, void *dst, const Plan &pl,
-                          const Grid &gd,
-                          const Coef<double> &k, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
-                          bool force, cudaStream_t s);
+                          const Grid &gd, const Coef<double> &k, void *snap, double2 *partials, DevStatus *st,
+                          bool drho, bool epi, bool force, int rev, cudaStream_t s);
 };
 
 struct DtypeOps {

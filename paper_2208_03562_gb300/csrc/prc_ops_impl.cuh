@@ -20,6 +20,7 @@ struct TmaArgs {
     float *sn;
     double2 *partials;
     DevStatus *st;
+    int rev;  // tile order of this step
 };
 
 template <int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
@@ -27,7 +28,8 @@ cudaError_t launch_tma_t(const TmaArgs &x, const Plan &pl, const Grid &gd, cudaS
 {
     using Cf = TmaCfg<S, W, H, THREADS>;
     k_step_tma<S, W, H, THREADS, MINB, DRHO, EPI, FORCE><<<pl.n_int_ctas, THREADS, Cf::SMEM, s>>>(
-        *x.tsrc, *x.tdst, x.a, x.b, gd, x.k, x.kf, x.sn, x.partials, x.st, pl.in, pl.edge);
+        *x.tsrc, *x.tdst, x.a, x.b, gd, x.k, x.kf, x.sn, x.partials, x.st, Interior{pl.in.ix0, pl.in.iy0, pl.in.ntx,
+        pl.in.nty, pl.in.xlast, pl.in.ylast, x.rev}, pl.edge);
     return cudaGetLastError();
 }
 
@@ -42,10 +44,10 @@ template <int W, int H, int THREADS, int MINB>
 cudaError_t launch_tma(const CUtensorMap *tsrc, const CUtensorMap *tdst, const void *src, void *dst, const Plan &pl,
                        const Grid &gd,
                        const Coef<double> &kd, void *snap, double2 *partials, DevStatus *st, bool drho, bool epi,
-                       bool force, cudaStream_t s)
+                       bool force, int rev, cudaStream_t s)
 {
     const TmaArgs x{tsrc, tdst, static_cast<const S *>(src), static_cast<S *>(dst), cast_coef<F2>(kd),
-                    cast_coef<float>(kd), static_cast<float *>(snap), partials, st};
+                    cast_coef<float>(kd), static_cast<float *>(snap), partials, st, rev};
     if (drho) {
         if (epi) return launch_tma_f<W, H, THREADS, MINB, true, true>(x, pl, gd, force, s);
         return launch_tma_f<W, H, THREADS, MINB, true, false>(x, pl, gd, force, s);

@@ -95,6 +95,7 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 struct Interior {
     int ix0, iy0, ntx, nty;
     int xlast, ylast;
+    int rev;  // take the tiles in reverse order (alternate steps, see k_step_tma)
 };
 
 template <typename S, int W_, int H_, int THREADS_ = 512>
@@ -235,15 +236,20 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
         for (int i = 0; i < 9; i++) tma_load_3d(stg + i * PE, &tsrc, b, x0 - C::PADX, y0 - 1 - ey_of(i), i);
     };
 
+    // Alternate steps take the tiles in opposite orders, so that a step first
+    // reads what the previous one wrote last, while it is still in L2.  `tile`
+    // runs over positions in the order; order(q) is the tile at position q.
+    auto order = [&](int q) { return in.rev ? ntiles - 1 - q : q; };
     RedAcc<float> acc;
     int tile = blockIdx.x;
     if (tid == 0) {
-        if (tile < ntiles) issue(tile, stage0, &bar[0]);
-        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, stage1, &bar[1]);
+        if (tile < ntiles) issue(order(tile), stage0, &bar[0]);
+        if (tile + (int)gridDim.x < ntiles) issue(order(tile + gridDim.x), stage1, &bar[1]);
     }
     // tile coordinates of this CTA's current tile, advanced by gridDim.x
     // tiles per iteration without a division
-    int tcx = blockIdx.x % in.ntx, tcy = blockIdx.x / in.ntx;
+    const int first = order(blockIdx.x);
+    int tcx = first % in.ntx, tcy = first / in.ntx;
     const int sdx = gridDim.x % in.ntx, sdy = gridDim.x / in.ntx;
     int px0 = 0, py0 = 0;  // origin of the previous tile (its TMA store is issued one tile later)
     int it = 0;
@@ -253,11 +259,20 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
         float *Rs = R + s * RF;
         const int ox = in.ix0 + tcx * W, oy = in.iy0 + tcy * H;
         const int x0 = min(ox, in.xlast), y0 = min(oy, in.ylast);
-        tcx += sdx;
-        tcy += sdy;
-        if (tcx >= in.ntx) {
-            tcx -= in.ntx;
-            tcy++;
+        if (!in.rev) {
+            tcx += sdx;
+            tcy += sdy;
+            if (tcx >= in.ntx) {
+                tcx -= in.ntx;
+                tcy++;
+            }
+        } else {
+            tcx -= sdx;
+            tcy -= sdy;
+            if (tcx < 0) {
+                tcx += in.ntx;
+                tcy--;
+            }
         }
         const bool own_x = x0 + x >= ox;  // the pair's column is owned by this tile
         float2 snv[C::NQ];
@@ -323,7 +338,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
             return;
         }
         if (tid == 0) {
-            if (tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, cur, &bar[s]);
+            if (tile + 2 * (int)gridDim.x < ntiles) issue(order(tile + 2 * gridDim.x), cur, &bar[s]);
             if constexpr (C::TSTORE) {
                 // store the previous tile: every thread wrote and fenced its
                 // part of the output buffer before the barrier above
