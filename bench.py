@@ -272,20 +272,30 @@ def e2e_leg(steps, torch, L):
 
 def ttss_leg(L, budget_s=150.0):
     """Time to steady state on the deep cavity (128 x 128, r = 2, Re = 1000,
-    Ma = 0.06): the preconditioned FP32 path (gamma = 0.1) and the plain FP64
-    path (gamma = 1, no preconditioning), both single-instance handles run to
-    residual 1e-6 (Sec. 5.2), wall time from the first step to the step that
-    met the residual, with the residual checks included."""
+    Ma = 0.06), to residual 1e-6 (Sec. 5.2), wall time from the first step to
+    the step that met the residual, with the residual checks included:
+    - the preconditioned FP32 path (gamma = 0.1), a single-instance handle;
+    - the FP16 -> FP32 precision schedule (gamma = 0.1) through the solve
+      server (batch engine, stall test on the device) and on single-instance
+      handles (stall test on the host between launches);
+    - the plain FP64 path (gamma = 1, no preconditioning)."""
     from paper_2208_03562_gb300 import inputs as I
     import time as _t
     out = {"workload": "deep lid-driven cavity 128x128, r=2 (H/L=2), Re=1000, Ma=0.06, from rest",
            "tol": 1e-6}
     for name, dt, gamma, bud in (("f32_gamma0.1", L.F32, 0.1, budget_s / 3),
                                  ("f16_to_f32_gamma0.1", None, 0.1, budget_s / 3),
+                                 ("f16_to_f32_gamma0.1_single", "single", 0.1, budget_s / 3),
                                  ("f64_plain_gamma1", L.F64, 1.0, budget_s)):
         cav = I.deep_cavity_128(gamma)
         t0 = _t.perf_counter()
         steps, st = 0, None
+        if dt == "single":  # the same schedule on single-instance handles (cluster engine)
+            from paper_2208_03562_gb300 import serve as SV
+            r = SV.solve_promoted(cav.nx, cav.ny, cav.r, gamma, cav.nu, cav.u_lid, 1e-6, 20_000_000)
+            out[name] = {"status": r["status"], "steps": r["steps"], "steps_by_stage": r["steps_by_stage"],
+                         "s": _t.perf_counter() - t0, "residual": r.get("residual")}
+            continue
         if dt is None:  # FP16 storage until the residual stalls, then FP32
             from paper_2208_03562_gb300 import serve as SV
             srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=2, reserve_bytes=0, budget_bytes=1 << 30,

@@ -385,3 +385,53 @@ def gpu_server(stages: Sequence[Stage], capacity: int = 256, budget_bytes: Optio
 def fp16_schedule(stall_window: int = 2000, stall_ratio: float = 0.9) -> List[Stage]:
     """FP16 shifted storage until the residual stalls, then FP32 to the tolerance."""
     return [Stage(2, stall_window, stall_ratio), Stage(1)]
+
+
+def solve_promoted(nx: int, ny: int, r: float, gamma: float, nu: float, u_lid: float, tol: float,
+                   max_steps: int, stall_window: int = 2000, stall_ratio: float = 0.9) -> dict:
+    """One steady-state solve with the FP16 -> FP32 precision schedule on
+    single-instance handles (the cluster engine for small grids): FP16
+    storage until the residual stalls -- at a check `stall_window` steps
+    after the previous one the residual is above `stall_ratio` times that
+    one's -- then the state moves to an FP32 handle with the initial mass
+    restored, which runs to `tol`.  The same rule as the batch's stall test,
+    applied on the host between launches."""
+    from . import lbm as L
+    L.load()
+    g = L.Lbm(L.lbm_params_init(nx, ny, r, gamma, nu, u_lid, L.F16))
+    mass0 = float(nx * ny)  # the rest start
+    steps16, prev, status = 0, None, None
+    try:
+        while steps16 < max_steps:
+            st, n = g.run(tol, min(stall_window, max_steps - steps16))
+            steps16 += n
+            status = st
+            if st == L.OK:
+                break
+            res = g.residual()
+            if prev is not None and res > stall_ratio * prev:
+                break  # stalled at the FP16 floor
+            prev = res
+    except L.LbmError as e:
+        g.close()
+        return {"status": "diverged" if e.status == L.EDIVERGED else "error", "steps": steps16,
+                "steps_by_stage": [steps16, 0]}
+    if status == L.OK:
+        res = g.residual()
+        g.close()
+        return {"status": "converged", "steps": steps16, "steps_by_stage": [steps16, 0], "residual": res}
+    f = g.populations()
+    g.close()
+    h = L.Lbm(L.lbm_params_init(nx, ny, r, gamma, nu, u_lid, L.F32))
+    h.set_populations(f)
+    h.set_mass(mass0)
+    try:
+        st, n = h.run(tol, max_steps - steps16)
+    except L.LbmError as e:
+        h.close()
+        return {"status": "diverged" if e.status == L.EDIVERGED else "error", "steps": steps16,
+                "steps_by_stage": [steps16, 0]}
+    out = {"status": "converged" if st == L.OK else "not converged", "steps": steps16 + n,
+           "steps_by_stage": [steps16, n], "residual": h.residual(), "fields": h.fields()}
+    h.close()
+    return out
