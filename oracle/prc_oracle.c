@@ -40,7 +40,9 @@
  *       source lies above the top wall takes the top wall's velocity.
  *   A4  R_2s, R_2d: App. A drops the (1/gamma - 1) terms and flips the sign
  *       of e_s,rho relative to Eq. 45; Eq. 45 (which follows from Eqs. 41-42
- *       and the definition of the non-equilibrium moments) is used.
+ *       and the definition of the non-equilibrium moments) is used.  The
+ *       parameter appendix_literal takes App. A's form instead, so that the
+ *       effect of this reading can be measured.
  *   A5  The App. A list of F^-1 writes central moments on the left; read as
  *       raw = binomial expansion of the central moments.
  *   A6  lambda_3y printed twice in App. A is lambda_by and lambda_sy.
@@ -86,6 +88,9 @@ typedef struct {
     int corrections; /* 1: extended equilibria (Eq. 30-40); 0: Eq. 14    */
     int model;       /* 0: PRC-LBM (central moments, Sec. 4.2, App. A);
                         1: PRNR-LBM (raw moments, Sec. 4.1 and Sec. 5.3)   */
+    int appendix_literal; /* 1: the strain-rate residuals exactly as App. A
+                             prints them (reading A4 not applied); for
+                             reporting the size of that reading only    */
 } orc_params;
 
 /* Per-run constants derived once from the parameters. */
@@ -250,9 +255,15 @@ static void collide(const orc_consts *c, const double f[9], double dxrho, double
         double B = 0.5 * (Ug * cs2 - r * r) * uy;
         double e_brho = -A * dxrho - B * dyrho;
         double e_srho = -A * dxrho + B * dyrho;
-        /* reading A4: Eq. 45 */
-        double R2s = c2s - 2 * cs2 * rho - (1.0 / g - 1.0) * (ux2 + uy2) * rho + e_brho;
-        double R2d = c2d - (1.0 / g - 1.0) * (ux2 - uy2) * rho + e_srho;
+        /* reading A4: Eq. 45; with appendix_literal, App. A's residuals */
+        double R2s, R2d;
+        if (p->appendix_literal) {
+            R2s = c2s - 2 * cs2 * rho + e_brho;
+            R2d = c2d - e_srho;
+        } else {
+            R2s = c2s - 2 * cs2 * rho - (1.0 / g - 1.0) * (ux2 + uy2) * rho + e_brho;
+            R2d = c2d - (1.0 / g - 1.0) * (ux2 - uy2) * rho + e_srho;
+        }
         double Cbx = (-2 * cs2 / wxi + (Pg * ux2 + Qg * uy2) / 2 + (3 * cs2 - 1.0) / 2) * rho;
         double Cby = (-2 * cs2 / wxi + (Pg * uy2 + Qg * ux2) / 2 + (3 * cs2 - r * r) / 2) * rho;
         double Csx = (-2 * cs2 / wnu + (Pg * ux2 - Qg * uy2) / 2 + (3 * cs2 - 1.0) / 2) * rho;

@@ -23,6 +23,7 @@ class _Params(C.Structure):
         ("omega_12", C.c_double), ("omega_22", C.c_double),
         ("fx", C.c_double), ("fy", C.c_double),
         ("bc", C.c_int), ("drho_off", C.c_int), ("corrections", C.c_int), ("model", C.c_int),
+        ("appendix_literal", C.c_int),
     ]
 
 
@@ -46,6 +47,7 @@ class OracleParams:
     drho_off: int = 0
     corrections: int = 1
     model: int = 0  # 0: PRC-LBM (central moments); 1: PRNR-LBM (raw moments)
+    appendix_literal: int = 0  # 1: App. A's strain-rate residuals as printed (reading A4 not applied)
 
     def c(self) -> _Params:
         d = asdict(self)

@@ -532,3 +532,45 @@ def test_staggered_modes_survive_in_the_steady_state():
     dx, dy = bx - ax, by - ay
     corr = lambda d, m: abs(np.sum(d * m)) / math.sqrt(np.sum(d * d) * np.sum(m * m))
     assert corr(dx, (-1.0) ** X) > 0.5 and corr(dy, (-1.0) ** Y) > 0.4
+
+
+# ---------------------------------------------------------------------------
+# Reading A4: the strain-rate residuals of Eq. 45 against App. A as printed
+
+
+def _a4_run(appendix_literal, gamma, drho_off, steps):
+    from paper_2208_03562_gb300 import inputs as I
+    o = S.Oracle(S.OracleParams(nx=48, ny=24, r=0.5, gamma=gamma, nu=0.01, u_lid=0.03, drho_off=drho_off,
+                                appendix_literal=appendix_literal))
+    w = S.rest_weights(o.p)[:, None, None]
+    o.set_populations(w + I.noise(5, (9, 24, 48), 1e-3))
+    o.step(steps)
+    return o.populations()
+
+
+def test_appendix_residuals_coincide_with_eq45_where_they_must():
+    """At gamma = 1 without density-gradient terms the (1/gamma - 1) terms and
+    e_s,rho vanish, so App. A's residuals and Eq. 45 give the same run; with
+    gamma < 1 they differ."""
+    assert np.array_equal(_a4_run(0, 1.0, 1, 100), _a4_run(1, 1.0, 1, 100))
+    assert np.max(np.abs(_a4_run(0, 0.25, 1, 100) - _a4_run(1, 0.25, 1, 100))) > 1e-4
+
+
+def test_reading_a4_keeps_the_steady_state_independent_of_gamma():
+    """Preconditioning must leave the steady state unchanged up to the
+    O(Ma^2 / gamma) compressibility error (Sec. 5.2).  With Eq. 45's
+    residuals the gamma = 0.25 cavity settles about half as far from the
+    gamma = 1 solution as with App. A's residuals as printed (measured
+    2.6 % against 5.2 % relative L2 of u)."""
+    def steady(lit, gamma):
+        o = S.Oracle(S.OracleParams(nx=64, ny=32, r=0.5, gamma=gamma, nu=0.05 * 32 * 0.5 / 100, u_lid=0.05,
+                                    appendix_literal=lit))
+        o.run(1e-10, 800000)
+        return o.fields()
+
+    def rel(a, b):
+        return np.sqrt(np.sum((a[1] - b[1]) ** 2 + (a[2] - b[2]) ** 2) / np.sum(b[1] ** 2 + b[2] ** 2))
+
+    ref = steady(0, 1.0)
+    d45, dapp = rel(steady(0, 0.25), ref), rel(steady(1, 0.25), ref)
+    assert d45 < 0.7 * dapp, (d45, dapp)
