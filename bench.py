@@ -383,12 +383,13 @@ def serve_leg(L, budget_s=60.0, n=64, scale=4):
     return sm
 
 
-def oracle_sample_rate(nx, ny, steps_budget_s=12.0, max_steps=200):
-    """The FP64 oracle on the host cores on a slab of the workload."""
+def oracle_sample_rate(nx, ny, steps_budget_s=12.0, max_steps=200, threads=0):
+    """The FP64 oracle on a slab of the workload, on `threads` host cores
+    (0: every core this process may use)."""
     from oracle import stepper as S
     from paper_2208_03562_gb300 import inputs as I
     cav = I.shallow_cavity_8192x2048("f64")
-    threads = S.num_threads(len(os.sched_getaffinity(0)))
+    threads = S.num_threads(threads if threads > 0 else len(os.sched_getaffinity(0)))
     o = S.Oracle(S.OracleParams(nx=nx, ny=ny, r=cav.r, gamma=cav.gamma, nu=cav.nu, u_lid=cav.u_lid))
     t = time.perf_counter()
     o.step(1)
@@ -497,10 +498,14 @@ def main():
                 line[key] = fn(L)
             except Exception as e:  # reported, not hidden
                 line[key] = {"error": repr(e)}
+        v1, _, steps1, dt1 = oracle_sample_rate(8192, 8, steps_budget_s=3.0, max_steps=100, threads=1)
         v, threads, steps, dt = oracle_sample_rate(8192, 64)
         line["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": threads, "kind": "oracle",
                                 "sample": "FP64 oracle on an 8192x64 slab of the workload, %d steps, %.1f s"
-                                          % (steps, dt)}
+                                          % (steps, dt),
+                                "single_core": {"value": v1, "unit": "GLUPS", "cores": 1,
+                                                "sample": "FP64 oracle on an 8192x8 slab, %d steps, %.1f s"
+                                                          % (steps1, dt1)}}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
