@@ -346,6 +346,19 @@ lbm_status lbm_batch_remove(lbm_batch_t b, int slot);
  * in the paper.  EINVAL for window < 0 or window > 0 with ratio <= 0.
  */
 lbm_status lbm_batch_set_stall(lbm_batch_t b, int slot, long window, double ratio);
+/*
+ * Check of the failure detection; no counterpart in the paper.  For the next
+ * lbm_batch_launch only:
+ *   cycles  the grid barrier between steps waits at most this many SM clock
+ *           cycles (0 keeps the default, about two seconds);
+ *   hold    != 0: the first CTA withholds its arrival at the first barrier,
+ *           so that every other CTA's wait runs out.
+ * A launch whose barrier wait runs out ends early: lbm_batch_wait (and
+ * lbm_batch_run) return LBM_ETIMEOUT, and the device stays usable.  With
+ * hold the launch stops at its first barrier, before any slot's step counter
+ * moves, so every slot keeps its state.  EINVAL for cycles < 0.
+ */
+lbm_status lbm_batch_set_wait_limit(lbm_batch_t b, long long cycles, int hold);
 /* Advance every active slot by up to `steps` steps (one persistent launch). */
 lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph);
 /* Wait for the launch; *n_active receives the slots still active. */

@@ -67,6 +67,8 @@ struct lbm_batch_s {
     bool in_flight;
     cudaGraphExec_t gexec;
     bool have_gexec;
+    long long next_limit;  // lbm_batch_set_wait_limit, for the next launch only
+    int next_hold;
     std::string err;
 };
 
@@ -271,6 +273,16 @@ lbm_status lbm_batch_set_stall(lbm_batch_t b, int slot, long window, double rati
     return LBM_OK;
 }
 
+lbm_status lbm_batch_set_wait_limit(lbm_batch_t b, long long cycles, int hold)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    if (cycles < 0) return bfail(b, LBM_EINVAL, "wait limit must be >= 0");
+    b->next_limit = cycles;
+    b->next_hold = hold != 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_remove(lbm_batch_t b, int slot)
 {
     lbm_status s = benter(b);
@@ -338,6 +350,14 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
     }
     BCK(b, cudaMemcpyAsync(b->d_inst, b->h_inst, n * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), b->stream));
+    if (b->next_limit > 0 || b->next_hold) {  // one launch only (lbm_batch_set_wait_limit)
+        std::memset(b->h_ctl, 0, sizeof(BatchCtl));
+        b->h_ctl->limit = b->next_limit;
+        b->h_ctl->hold = b->next_hold;
+        BCK(b, cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->stream));
+        b->next_limit = 0;
+        b->next_hold = 0;
+    }
     int grid = b->occupancy * b->num_sms;
     if (grid > tiles) grid = tiles;
     const int st = (int)steps;

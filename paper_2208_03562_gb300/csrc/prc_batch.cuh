@@ -78,7 +78,8 @@ struct BatchCtl {
     unsigned arrive;     // grid barrier
     unsigned gen;
     int error;           // 1: barrier timeout
-    int pad;
+    int hold;            // failure-detection check: CTA 0 withholds its first arrival
+    long long limit;     // wait limit of the grid barrier in SM clock cycles (0: about two seconds)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
@@ -106,7 +107,16 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl)
         const unsigned g = ld_acquire_u32(&ctl->gen);
         __threadfence();
         const unsigned n = gridDim.x;
-        if (atomicAdd(&ctl->arrive, 1u) == n - 1) {
+        const long long limit = ctl->limit > 0 ? ctl->limit : 4000000000LL;  // about two seconds by default
+        // (check of the failure detection) CTA 0 withholds its arrival, so
+        // that every other CTA's wait runs out; it then waits out its own
+        if (ctl->hold && blockIdx.x == 0) {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&ctl->gen) == g && !ld_relaxed_i32(&ctl->error) && clock64() - t0 <= limit)
+                __nanosleep(64);
+            atomicExch(&ctl->error, 1);
+            ok = 0;
+        } else if (atomicAdd(&ctl->arrive, 1u) == n - 1) {
             atomicExch(&ctl->arrive, 0u);
             __threadfence();
             atomicAdd(&ctl->gen, 1u);
@@ -117,7 +127,7 @@ __device__ __forceinline__ bool grid_barrier(BatchCtl *ctl)
                     ok = 0;
                     break;
                 }
-                if (clock64() - t0 > 4000000000LL) {  // about two seconds
+                if (clock64() - t0 > limit) {
                     atomicExch(&ctl->error, 1);
                     ok = 0;
                     break;

@@ -95,6 +95,7 @@ def load():
         "lbm_batch_add": [B, P, C.c_double, C.c_long, C.POINTER(C.c_int)],
         "lbm_batch_remove": [B, C.c_int],
         "lbm_batch_set_stall": [B, C.c_int, C.c_long, C.c_double],
+        "lbm_batch_set_wait_limit": [B, C.c_longlong, C.c_int],
         "lbm_batch_launch": [B, C.c_long, C.c_int],
         "lbm_batch_wait": [B, C.POINTER(C.c_int)],
         "lbm_batch_run": [B, C.c_long, C.POINTER(C.c_int)],
@@ -132,7 +133,7 @@ def exported_symbols():
                  "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
                  "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc", "lbm_batch_create",
                  "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_instance_bytes", "lbm_batch_add",
-                 "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
+                 "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_set_wait_limit", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
                  "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations",
                  "lbm_batch_mass", "lbm_batch_set_mass", "lbm_set_mass"):
         if hasattr(L, name):
@@ -478,6 +479,12 @@ class Batch:
         """Retire the slot as STALLED when its residual stops falling (see
         lbm_batch_set_stall); window = 0 turns the test off."""
         _bcheck(load().lbm_batch_set_stall(self.b, slot, int(window), float(ratio)), self.b)
+
+    def set_wait_limit(self, cycles: int, hold: bool = False):
+        """For the next launch only: the grid-barrier wait limit in SM cycles
+        (0: the default) and, with hold, a withheld arrival that makes the
+        waits run out (lbm_batch_set_wait_limit)."""
+        _bcheck(load().lbm_batch_set_wait_limit(self.b, int(cycles), 1 if hold else 0), self.b)
 
     def launch(self, steps: int, use_graph: bool = True):
         _bcheck(load().lbm_batch_launch(self.b, int(steps), 1 if use_graph else 0), self.b)

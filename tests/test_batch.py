@@ -157,3 +157,39 @@ def test_add_and_remove_between_launches():
         b.add(mk(20, 20), 1e-30, 10 ** 6)
     assert e.value.status == L.ENOMEM
     b.remove(s3)
+
+
+def test_grid_barrier_wait_runs_out_and_reports_timeout():
+    """Failure detection without a fault: the first CTA withholds its arrival
+    at the first grid barrier (a flag that nothing clears), every other CTA's
+    bounded wait runs out (limit about 1 ms), the launch ends with
+    LBM_ETIMEOUT, no slot's state has moved, and the device and the batch
+    stay usable: the next launch steps as if the failed one had not been."""
+    mk = lambda nx, ny: L.lbm_params_init(nx, ny, 0.5, 0.3, 0.01, 0.03, L.F32)
+    b = L.Batch(2, L.F32)
+    s0 = b.add(mk(64, 32), 1e-30, 10 ** 6)
+    s1 = b.add(mk(200, 90), 1e-30, 10 ** 6)
+    f0 = [b.populations(s) for s in (s0, s1)]
+    b.set_wait_limit(2_000_000, hold=True)
+    with pytest.raises(L.LbmError) as e:
+        b.run(50)
+    assert e.value.status == L.ETIMEOUT
+    for s, f in zip((s0, s1), f0):
+        info, st = b.query(s)
+        assert st == L.SLOT_ACTIVE and info.step == 0
+        assert np.array_equal(b.populations(s), f)
+    assert b.run(40) == 2  # the default limit again, one launch only
+    for s, (nx, ny) in zip((s0, s1), ((64, 32), (200, 90))):
+        h = L.Lbm(mk(nx, ny))
+        h.variant = L.VARIANT_GENERAL
+        h.step(40)
+        info, st = b.query(s)
+        assert info.step == 40 and np.array_equal(b.populations(s), h.populations())
+        h.close()
+
+
+def test_wait_limit_rejects_negative_cycles():
+    b = L.Batch(1, L.F32)
+    with pytest.raises(L.LbmError) as e:
+        b.set_wait_limit(-1)
+    assert e.value.status == L.EINVAL
