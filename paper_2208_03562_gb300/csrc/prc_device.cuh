@@ -35,20 +35,20 @@ template <typename T>
 struct Coef {
     T r, r2;                   // aspect ratio r = dy/dx, r^2
     T c2, c4;                  // c^2 = q^2 c_s*^2, q = min(1, r) (Eq. 2); c^4
-    T ig, h1, hh1;             // 1/g, 1/g - 1, (1/g - 1)/2
-    T one_m_w_nu;              // 1 - omega_nu
-    T hxi, hnu;                // (1 - omega_xi)/2, (1 - omega_nu)/2
-    T kxs, kd;                 // -omega_xi tau_xi, -omega_nu tau_nu (tau = 1/omega - 1/2)
-    T Qg, hPg, hQg;            // Q_gamma, P_gamma / 2, Q_gamma / 2
+    T hh1;                     // (1/g - 1)/2
     T Ax, By;                  // A = Ax u_x, B = By u_y (Eq. 43)
-    T k3x, k3y;                // (3c^2 - 1)/2, (3c^2 - r^2)/2
-    T Cb0, Cs0;                // -2 c^2 / omega_xi, -2 c^2 / omega_nu
-    T h1c2;                    // (1/g - 1) c^2
+    T pp, npp, pm;             // (P_gamma + Q_gamma)/4, its negation, (P_gamma - Q_gamma)/4
+    T e1, e2, ne2, e3;         // strain-rate system constants: Cb0 + k3, k3d, -k3d, Cs0 + k3
+    T kS, kD;                  // omega_xi tau_xi Cb0, omega_nu tau_nu Cs0
+    T h1x2, omw2;              // 2 (1/g - 1), 2 (1 - omega_nu)
+    T kdQg2, kdh1c2x2;         // -2 omega_nu tau_nu Q_gamma, -2 omega_nu tau_nu (1/g - 1) c^2
     T a3p1, a34p1;             // a3 + 1, 4 a3 + 1 with a3 = 1/g^2 - 3/g + 2
     T qr, qr2, hr, hr2, inv_r2;  // 1/(4r), 1/(4r^2), 1/(2r), 1/(2r^2), 1/r^2
+    T n2qr, n2qr2;             // -1/(2r), -1/(2r^2)
     T hx, hy;                  // F / (2 gamma): half-force velocity shift
-    T fsx, fsy, fdx, fdy;      // (1 - omega/2) Q_gamma F: source moments (Eq. 13-central)
-    T nig, nr2, nhPg, nhQg, nk3y, ninv_r2, nfdy;  // negated copies
+    T fsx, fsy, fdx, nfdy;     // (1 - omega/2) Q_gamma F: source moments (Eq. 13-central)
+    T fdx2, fdy2;              // 2 fdx, 2 fdy
+    T nig, nr2, ninv_r2;       // -1/g, -r^2, -1/r^2
     T lid;                     // c^2 U / (2 r^2): moving-lid bounce-back term
     T ig2;                     // 1 / g^2 (raw-moment scheme)
     T inv12, inv12r;           // 1/12, 1/(12 r): density-gradient stencil
@@ -144,10 +144,15 @@ __device__ __forceinline__ void pull9(const S *__restrict__ src, const Grid &gd,
     }
 }
 
+// Density deviation sum_i g_i, summed in the order the collision forms s00
+// (same operands, same pairing), so that a kernel which takes the density
+// before a barrier and collides after it computes those sums once.
 template <typename T>
 PRC_HD T sum9(const T g[9])
 {
-    return vadd(vadd(vadd(vadd(g[0], g[1]), vadd(g[2], g[3])), vadd(vadd(g[4], g[5]), vadd(g[6], g[7]))), g[8]);
+    const T p13 = vadd(g[1], g[3]), p24 = vadd(g[2], g[4]);
+    const T d58 = vadd(vadd(g[5], g[6]), vadd(g[7], g[8]));
+    return vadd(vadd(g[0], d58), vadd(p13, p24));
 }
 
 // The collision in deviation form (App. A with the algebra rearranged as in
@@ -208,43 +213,50 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
         nesr = vsub(Adx, Bdy);
     }
     const T R2s = vsub(n2s, nebr), R2d = vsub(n2d, nesr);
-    const T ax = vmul(vfma(k.hPg, ux2, vfma(k.hQg, uy2, k.k3x)), rho);
-    const T ay = vmul(vfma(k.hPg, uy2, vfma(k.hQg, ux2, k.k3y)), rho);
-    const T dx = vmul(vfma(k.hPg, ux2, vfma(k.nhQg, uy2, k.k3x)), rho);
-    const T ndy = vmul(vfma(k.nhPg, uy2, vfma(k.hQg, ux2, k.nk3y)), rho);
-    const T Cb0r = vmul(k.Cb0, rho), Cs0r = vmul(k.Cs0, rho);
-    const T Cbx = vadd(Cb0r, ax), Cby = vadd(Cb0r, ay);
-    const T Csx = vadd(Cs0r, dx), Csy = vsub(ndy, Cs0r);
-    const T det = vsub(vmul(Cbx, Csy), vmul(Csx, Cby));
-    const T X = vmul(vsub(vmul(Csy, R2s), vmul(Cby, R2d)), vrcp(det));
-    const T Y = vmul(vsub(R2s, vmul(Cbx, X)), vrcp(Cby));
+    // The two unknowns X, Y of the strain-rate system (Eqs. 43-44) solve
+    //   (Cb0 rho + a_x) X + (Cb0 rho + a_y) Y = R2s,
+    //   (Cs0 rho + d_x) X + (d_y' - Cs0 rho) Y = R2d,
+    // with a_x = rho (k3x + P u_x^2 / 2 + Q u_y^2 / 2) and the like.  The
+    // system is homogeneous in rho, and the moments below use X and Y only as
+    // Xs = rho (X + Y) and Xd = rho (X - Y): by the two rows, the corrections
+    // a_x X + a_y Y + e_b and d_x X + d_y' Y + e_s are n2s - Cb0 Xs and
+    // n2d - Cs0 Xd.  So the system is solved for (Xs, Xd) directly, with
+    // rho = 1 and its coefficients taken half:
+    //   m11 = Cb0 + (k3x + k3y)/2 + (P + Q)/4 (u_x^2 + u_y^2),
+    //   m12 = (k3x - k3y)/2 + (P - Q)/4 (u_x^2 - u_y^2),
+    //   m21 = (k3x - k3y)/2 + (P + Q)/4 (u_x^2 - u_y^2),
+    //   m22 = Cs0 + (k3x + k3y)/2 + (P - Q)/4 (u_x^2 + u_y^2).
+    const T qp = vadd(ux2, uy2), qm = vsub(ux2, uy2);
+    const T m11 = vfma(k.pp, qp, k.e1), m22 = vfma(k.pm, qp, k.e3);
+    const T m12 = vfma(k.pm, qm, k.e2), nm21 = vfma(k.npp, qm, k.ne2);
+    const T idet = vrcp(vfma(m11, m22, vmul(m12, nm21)));
+    const T Xs = vmul(vsub(vmul(m22, R2s), vmul(m12, R2d)), idet);
+    const T Xd = vmul(vfma(m11, R2d, vmul(nm21, R2s)), idet);
 
-    // extended-equilibrium corrections (Eqs. 30, 38-40 / App. A) and relaxation;
-    // hdt2s = (k~2s - 2 c^2 rho) / 2, ht2d = k~2d / 2
-    const T cs = vfma(ax, X, vfma(ay, Y, nebr));
-    const T cd = vfma(dx, X, vfma(ndy, Y, nesr));
-    T c11 = vmul(vmul(k.Qg, ruxy), vadd(X, Y));
-    if (DRHO) c11 = vfma(k.h1c2, vfma(uy, dxr, vmul(ux, dyr)), c11);
-    T hdt2s = vfma(k.hh1, sp, vfma(k.hxi, n2s, vmul(k.kxs, cs)));
-    T ht2d = vfma(k.hh1, sm, vfma(k.hnu, n2d, vmul(k.kd, cd)));
-    T t11 = vfma(k.h1, ruxy, vfma(k.one_m_w_nu, n11, vmul(k.kd, c11)));
+    // extended-equilibrium corrections (Eqs. 30, 38-40 / App. A) and
+    // relaxation.  Relaxing n2s at omega_xi and adding -omega_xi tau_xi times
+    // its correction n2s - Cb0 Xs leaves -n2s / 2 + omega_xi tau_xi Cb0 Xs
+    // ((1 - omega)/2 - omega tau = -1/2); likewise for n2d.
+    // b20 = c^2 s00 + (k~2s - 2 c^2 rho)/2, ht2d = k~2d / 2, t11x2 = 2 k~11
+    T b20 = vfma(k.hh1, sp, vfma(splat<T>(-0.5), n2s, vfma(k.kS, Xs, c2s00)));
+    T ht2d = vfma(k.hh1, sm, vfma(splat<T>(-0.5), n2d, vmul(k.kD, Xd)));
+    T t11x2 = vfma(k.h1x2, ruxy, vfma(k.omw2, n11, vmul(vmul(k.kdQg2, uxy), Xs)));
+    if (DRHO) t11x2 = vfma(k.kdh1c2x2, vfma(uy, dxr, vmul(ux, dyr)), t11x2);
     if (FORCE) {
-        hdt2s = vfma(k.fsx, ux, vfma(k.fsy, uy, hdt2s));
+        b20 = vfma(k.fsx, ux, vfma(k.fsy, uy, b20));
         ht2d = vfma(k.fdx, ux, vfma(k.nfdy, uy, ht2d));
-        t11 = vfma(k.fdx, uy, vfma(k.fdy, ux, t11));
+        t11x2 = vfma(k.fdx2, uy, vfma(k.fdy2, ux, t11x2));
     }
-    const T dt20 = vadd(hdt2s, ht2d);  // k~20 - c^2 rho
-    const T dt02 = vsub(hdt2s, ht2d);  // k~02 - c^2 rho
-    const T c2rho = vmul(k.c2, rho);
-    const T t20 = vadd(c2rho, dt20), t02 = vadd(c2rho, dt02);
+    const T E20 = vadd(b20, ht2d), E02 = vsub(b20, ht2d);  // c^2 s00 + k~20 - c^2 rho, and for 02
+    const T t20 = vadd(E20, k.c2), t02 = vadd(E02, k.c2);   // k~20, k~02 (c^2 rho = c^2 + c^2 s00)
 
     // post-collision raw moments minus the rest-state moments (F^-1), with
     // k~21 = a3 rho u_x^2 u_y, k~12 = a3 rho u_x u_y^2, k~22 = c^4 rho
     const T e21 = vmul(rux2, uy), e12 = vmul(ruy2, ux);
     T D10 = jx, D01 = jy;
-    T D20 = vadd(vadd(c2s00, rux2), dt20);
-    T D02 = vadd(vadd(c2s00, ruy2), dt02);
-    T D11 = vadd(t11, ruxy);
+    T D20 = vadd(E20, rux2);
+    T D02 = vadd(E02, ruy2);
+    T D11 = vfma(splat<T>(0.5), t11x2, ruxy);
     T D21, D12, D22;
     if constexpr (RAW) {
         // raw equilibria of Eq. 12: rho (c^2 + u_x^2 / g^2) u_y, rho (c^2 +
@@ -253,9 +265,9 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
         D12 = vfma(k.c2, jx, vmul(k.ig2, e12));
         D22 = vfma(k.c4, s00, vfma(k.c2, sp, vmul(e21, uy)));
     } else {
-        D21 = vfma(k.a3p1, e21, vfma(vadd(ux, ux), t11, vmul(uy, t20)));
-        D12 = vfma(k.a3p1, e12, vfma(vadd(uy, uy), t11, vmul(ux, t02)));
-        D22 = vfma(ux2, t02, vfma(uy2, t20, vfma(vmul(splat<T>(4.0), uxy), t11,
+        D21 = vfma(k.a3p1, e21, vfma(ux, t11x2, vmul(uy, t20)));
+        D12 = vfma(k.a3p1, e12, vfma(uy, t11x2, vmul(ux, t02)));
+        D22 = vfma(ux2, t02, vfma(uy2, t20, vfma(vadd(uxy, uxy), t11x2,
                                                  vfma(k.a34p1, vmul(e21, uy), vmul(k.c4, s00)))));
     }
     if (FORCE) {
@@ -273,19 +285,21 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
     }
 
     // S^-1 then P^-1 (Eq. 72) with the 1/2, 1/4 and 1/r^n factors folded
-    const T Q11 = vmul(D11, k.qr), Q21 = vmul(D21, k.qr), Q12 = vmul(D12, k.qr2), Q22 = vmul(D22, k.qr2);
-    const T p = vadd(Q21, Q22), m = vadd(Q11, Q12), pp = vsub(Q22, Q21), mm = vsub(Q11, Q12);
+    // (Z21, Z12 = -2 Q21, -2 Q12 exactly: the scalings differ by a power of two)
+    const T Q11 = vmul(D11, k.qr), Q22 = vmul(D22, k.qr2), Z21 = vmul(D21, k.n2qr), Z12 = vmul(D12, k.n2qr2);
+    const T p = vfma(splat<T>(-0.5), Z21, Q22), m = vfma(splat<T>(-0.5), Z12, Q11);
+    const T pp = vfma(splat<T>(0.5), Z21, Q22), mm = vfma(splat<T>(0.5), Z12, Q11);
     g[5] = vadd(p, m);
     g[6] = vsub(p, m);
     g[7] = vadd(pp, mm);
     g[8] = vsub(pp, mm);
     const T n2Q22 = vmul(splat<T>(-2.0), Q22);
     const T a1 = vfma(splat<T>(0.5), D20, n2Q22);
-    const T b1 = vfma(splat<T>(0.5), D10, vmul(splat<T>(-2.0), Q12));
+    const T b1 = vfma(splat<T>(0.5), D10, Z12);
     g[1] = vadd(a1, b1);
     g[3] = vsub(a1, b1);
     const T a2 = vfma(k.hr2, D02, n2Q22);
-    const T b2 = vfma(k.hr, D01, vmul(splat<T>(-2.0), Q21));
+    const T b2 = vfma(k.hr, D01, Z21);
     g[2] = vadd(a2, b2);
     g[4] = vsub(a2, b2);
     g[0] = vfma(splat<T>(4.0), Q22, vfma(k.ninv_r2, D02, vsub(s00, D20)));

@@ -164,28 +164,30 @@ inline void make_coef(const lbm_params &p, Coef<double> &k)
     const double tau_nu = 1.0 / w_nu - 0.5, tau_xi = 1.0 / w_xi - 0.5;
     const double Pg = 4.0 / (g * g) - 1.0 / g, Qg = 1.0 / (g * g) - 1.0 / g, Ug = 2.0 / g + 1.0;
     const double a3 = 1.0 / (g * g) - 3.0 / g + 2.0;
+    const double k3x = 0.5 * (3.0 * c2 - 1.0), k3y = 0.5 * (3.0 * c2 - r * r);
+    const double Cb0 = -2.0 * c2 / w_xi, Cs0 = -2.0 * c2 / w_nu;
+    const double kd = -w_nu * tau_nu, kxs = -w_xi * tau_xi;
+    const double fdx = (1.0 - 0.5 * w_nu) * Qg * p.fx, fdy = (1.0 - 0.5 * w_nu) * Qg * p.fy;
     k.r = r;
     k.r2 = r * r;
     k.c2 = c2;
     k.c4 = c2 * c2;
-    k.ig = 1.0 / g;
-    k.h1 = 1.0 / g - 1.0;
-    k.hh1 = 0.5 * k.h1;
-    k.one_m_w_nu = 1.0 - w_nu;
-    k.hxi = 0.5 * (1.0 - w_xi);
-    k.hnu = 0.5 * (1.0 - w_nu);
-    k.kxs = -w_xi * tau_xi;
-    k.kd = -w_nu * tau_nu;
-    k.Qg = Qg;
-    k.hPg = 0.5 * Pg;
-    k.hQg = 0.5 * Qg;
+    k.hh1 = 0.5 * (1.0 / g - 1.0);
     k.Ax = 0.5 * (Ug * c2 - 1.0);
     k.By = 0.5 * (Ug * c2 - r * r);
-    k.k3x = 0.5 * (3.0 * c2 - 1.0);
-    k.k3y = 0.5 * (3.0 * c2 - r * r);
-    k.Cb0 = -2.0 * c2 / w_xi;
-    k.Cs0 = -2.0 * c2 / w_nu;
-    k.h1c2 = (1.0 / g - 1.0) * c2;
+    k.pp = 0.25 * (Pg + Qg);
+    k.npp = -k.pp;
+    k.pm = 0.25 * (Pg - Qg);
+    k.e1 = Cb0 + 0.5 * (k3x + k3y);
+    k.e2 = 0.5 * (k3x - k3y);
+    k.ne2 = -k.e2;
+    k.e3 = Cs0 + 0.5 * (k3x + k3y);
+    k.kS = -kxs * Cb0;
+    k.kD = -kd * Cs0;
+    k.h1x2 = 2.0 * (1.0 / g - 1.0);
+    k.omw2 = 2.0 * (1.0 - w_nu);
+    k.kdQg2 = 2.0 * kd * Qg;
+    k.kdh1c2x2 = 2.0 * kd * (1.0 / g - 1.0) * c2;
     k.a3p1 = a3 + 1.0;
     k.a34p1 = 4.0 * a3 + 1.0;
     k.qr = 0.25 / r;
@@ -193,19 +195,19 @@ inline void make_coef(const lbm_params &p, Coef<double> &k)
     k.hr = 0.5 / r;
     k.hr2 = 0.5 / (r * r);
     k.inv_r2 = 1.0 / (r * r);
+    k.n2qr = -2.0 * k.qr;
+    k.n2qr2 = -2.0 * k.qr2;
     k.hx = p.fx / (2.0 * g);
     k.hy = p.fy / (2.0 * g);
     k.fsx = (1.0 - 0.5 * w_xi) * Qg * p.fx;
     k.fsy = (1.0 - 0.5 * w_xi) * Qg * p.fy;
-    k.fdx = (1.0 - 0.5 * w_nu) * Qg * p.fx;
-    k.fdy = (1.0 - 0.5 * w_nu) * Qg * p.fy;
-    k.nig = -k.ig;
+    k.fdx = fdx;
+    k.nfdy = -fdy;
+    k.fdx2 = 2.0 * fdx;
+    k.fdy2 = 2.0 * fdy;
+    k.nig = -1.0 / g;
     k.nr2 = -k.r2;
-    k.nhPg = -k.hPg;
-    k.nhQg = -k.hQg;
-    k.nk3y = -k.k3y;
     k.ninv_r2 = -k.inv_r2;
-    k.nfdy = -k.fdy;
     const bool lid_on = (p.bc != LBM_BC_PERIODIC) && (p.u_lid != 0.0);
     k.lid = lid_on ? c2 * p.u_lid / (2.0 * r * r) : 0.0;
     k.ig2 = 1.0 / (g * g);
