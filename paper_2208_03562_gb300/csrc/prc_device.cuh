@@ -17,6 +17,9 @@
 //   * the non-equilibrium parts n_2s, n_2d, n_11 are formed from the
 //     deviation moments of g, e.g. n_20 = s20 - c^2 drho - rho u_x^2 / gamma
 //     + 2 u_x h_x;
+//   * the strain-rate system of Eqs. 43-44 is solved for rho (X + Y) and
+//     rho (X - Y), the only combinations the relaxed moments use (see the
+//     comments in collide);
 //   * post-collision raw moments are assembled minus the rest-state moments
 //     (1, 0, 0, c^2, c^2, 0, 0, 0, c^4), so P^-1 S^-1 of them is g~ directly.
 #pragma once
