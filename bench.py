@@ -44,6 +44,9 @@ def parse():
                     help="profiling only: use this interior-kernel variant instead of autotuning")
     ap.add_argument("--nx", type=int, default=0, help="profiling only: override the grid width")
     ap.add_argument("--ny", type=int, default=0, help="profiling only: override the grid height")
+    ap.add_argument("--profile-case", default="", choices=["", "batch", "cluster"],
+                    help="profiling only: run one small fixed case of the batch engine or the cluster engine "
+                         "(for an ncu capture of k_batch / k_cluster) and exit")
     return ap.parse_args()
 
 
@@ -351,6 +354,7 @@ def batch_leg(L, budget_s=30.0, n=256):
     for c in cavs:
         p = L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
         slots.append((b.add(p, c.tol, c.max_steps), c.nodes))
+    best, ms = b.autotune(20)  # persistent-grid size; the slots' state is restored
     t0 = _t.perf_counter()
     launches, active = 0, n
     while active and _t.perf_counter() - t0 < budget_s:
@@ -366,6 +370,7 @@ def batch_leg(L, budget_s=30.0, n=256):
     return {"workload": "%d cavities, nx 64..1024, ny 32..512, r in {0.25,0.5,1,2}, gamma 0.05..1, Re 100..5000, "
                         "FP32, residual 1e-7 (seed 0)" % n,
             "aggregate_glups": ns / dt / 1e9, "wall_s": dt, "launches": launches, "states": states,
+            "autotune": {"ctas_per_sm": best, "ms_per_step": ms},
             "note": "time-bounded: slots still ACTIVE had not reached 1e-7 when the budget ran out"}
 
 
@@ -439,8 +444,44 @@ def reference_main(args):
     return 0
 
 
+def profile_case(name):
+    """Profiling only: a small fixed workload of one engine, two launches, for
+    an ncu capture of the second (`-k regex:k_batch` or `regex:k_cluster`,
+    `-s 1 -c 1`).
+    batch: the first 24 cavities of the batched-sweep mix (FP32, 4.3 M
+    nodes, both population sets 311 MB > L2), launches of 20 and 60 steps.
+    cluster: the 128 x 128 deep cavity (r = 2, gamma = 0.1, FP32), launches of
+    200 and 2000 steps."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2208_03562_gb300 import lbm as L, inputs as I
+    L.load()
+    if name == "batch":
+        mix = I.batched_sweep(seed=0, n=256, dtype="f32")[:24]
+        b = L.Batch(len(mix), L.F32)
+        for c in mix:
+            b.add(L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32), 1e-30, 10 ** 6)
+        b.run(20)
+        b.run(60)
+        b.close()
+        out = {"profile_case": name, "slots": len(mix), "nodes": sum(c.nodes for c in mix), "steps": [20, 60]}
+    else:
+        cav = I.deep_cavity_128(0.1)
+        h = L.Lbm(L.lbm_params_init(cav.nx, cav.ny, cav.r, 0.1, cav.nu, cav.u_lid, L.F32))
+        if h.variant != L.VARIANT_CLUSTER:
+            raise RuntimeError("the 128 x 128 cavity did not select the cluster engine")
+        h.step(200)
+        h.step(2000)
+        h.sync()
+        out = {"profile_case": name, "nodes": cav.nodes, "steps": [200, 2000], "step_after": h.info().step}
+        h.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.nx or args.ny:
         GRID_OVERRIDE.update(nx=args.nx, ny=args.ny)
     if args.variant is not None:

@@ -359,6 +359,29 @@ lbm_status lbm_batch_set_stall(lbm_batch_t b, int slot, long window, double rati
  * moves, so every slot keeps its state.  EINVAL for cycles < 0.
  */
 lbm_status lbm_batch_set_wait_limit(lbm_batch_t b, long long cycles, int hold);
+/*
+ * Launch shape of the batch engine (no counterpart in the paper: it chooses
+ * how the same update is executed; a slot's results do not depend on it).
+ * The persistent grid of lbm_batch_launch is ctas_per_sm x (SM count) CTAs of
+ * the 64 x 8 tile body, capped at the number of tiles.
+ * lbm_batch_set_ctas_per_sm: 1 <= ctas_per_sm <= *max_ctas_per_sm of
+ * lbm_batch_get_ctas_per_sm (the resident CTAs per SM of the kernel), or 0
+ * for the default (the maximum); EINVAL otherwise.
+ * lbm_batch_autotune times `steps` steps (1 <= steps <= 100000) of the
+ * active slots at every ctas_per_sm from 1 to the maximum, each after one
+ * untimed launch of the same length, then restores every slot's populations,
+ * residual snapshot, step counter and state exactly and keeps the fastest
+ * choice.  *best receives it; ms_per_step[c - 1] receives the milliseconds per
+ * step at ctas_per_sm = c (room for *max_ctas_per_sm values).  Either pointer
+ * may be NULL.  Synchronous; it allocates a device copy of the slots' state
+ * for the restore (LBM_ENOMEM when that fails, with nothing changed).  With no
+ * active slot it times nothing and returns LBM_OK with *best = the current
+ * choice.  A timeout of the grid barrier during the timing returns
+ * LBM_ETIMEOUT after the restore.
+ */
+lbm_status lbm_batch_set_ctas_per_sm(lbm_batch_t b, int ctas_per_sm);
+lbm_status lbm_batch_get_ctas_per_sm(lbm_batch_t b, int *ctas_per_sm, int *max_ctas_per_sm);
+lbm_status lbm_batch_autotune(lbm_batch_t b, int steps, int *best, double *ms_per_step);
 /* Advance every active slot by up to `steps` steps (one persistent launch). */
 lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph);
 /* Wait for the launch; *n_active receives the slots still active. */

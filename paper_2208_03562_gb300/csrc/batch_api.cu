@@ -69,6 +69,7 @@ struct lbm_batch_s {
     bool have_gexec;
     long long next_limit;  // lbm_batch_set_wait_limit, for the next launch only
     int next_hold;
+    int ctas_per_sm;       // persistent grid: ctas_per_sm x SMs (0: occupancy)
     std::string err;
 };
 
@@ -358,7 +359,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         b->next_limit = 0;
         b->next_hold = 0;
     }
-    int grid = b->occupancy * b->num_sms;
+    int grid = (b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy) * b->num_sms;
     if (grid > tiles) grid = tiles;
     const int st = (int)steps;
     if (use_graph) {
@@ -391,6 +392,118 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
                                     spec, b->stream));
     }
     b->in_flight = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_ctas_per_sm(lbm_batch_t b, int ctas_per_sm)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    if (ctas_per_sm < 0 || ctas_per_sm > b->occupancy)
+        return bfail(b, LBM_EINVAL, "ctas_per_sm must be in [0, " + std::to_string(b->occupancy) + "]");
+    b->ctas_per_sm = ctas_per_sm;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_ctas_per_sm(lbm_batch_t b, int *ctas_per_sm, int *max_ctas_per_sm)
+{
+    if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
+    if (max_ctas_per_sm) *max_ctas_per_sm = b->occupancy;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch_t b, int steps, int *best, double *ms_per_step)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    if (b->in_flight) return bfail(b, LBM_EINVAL, "a launch is in flight: call lbm_batch_wait first");
+    if (steps < 1 || steps > 100000) return bfail(b, LBM_EINVAL, "steps must be in [1, 100000]");
+    const int current = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
+    // the state a launch changes: the active slots' memory and the dynamic table
+    std::vector<int> act;
+    size_t bytes = 0;
+    for (int i = 0; i < b->capacity; i++)
+        if (b->slots[i].used && b->h_dyn[i].state == prc::BATCH_ACTIVE) {
+            act.push_back(i);
+            bytes += slot_bytes(b->slots[i].L);
+        }
+    if (act.empty()) {
+        if (best) *best = current;
+        return LBM_OK;
+    }
+    const size_t dyn_bytes = (size_t)b->capacity * sizeof(BatchDyn);
+    char *save = nullptr;
+    if (cudaMallocAsync(&save, bytes + dyn_bytes, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LBM_ENOMEM, "device allocation of the state copy failed");
+    }
+    const std::vector<BatchDyn> h_save(b->h_dyn, b->h_dyn + b->capacity);
+    auto copy_state = [&](bool out) -> cudaError_t {
+        size_t off = 0;
+        for (int i : act) {
+            const size_t n = slot_bytes(b->slots[i].L);
+            void *dev = b->slots[i].mem;
+            cudaError_t e = out ? cudaMemcpyAsync(save + off, dev, n, cudaMemcpyDeviceToDevice, b->stream)
+                                : cudaMemcpyAsync(dev, save + off, n, cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) return e;
+            off += n;
+        }
+        if (!out) std::memcpy(b->h_dyn, h_save.data(), dyn_bytes);
+        return out ? cudaMemcpyAsync(save + bytes, b->d_dyn, dyn_bytes, cudaMemcpyDeviceToDevice, b->stream)
+                   : cudaMemcpyAsync(b->d_dyn, save + bytes, dyn_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    lbm_status rs = LBM_OK;
+    std::string msg;
+    int best_c = current;
+    double best_ms = 0.0;
+    if (copy_state(true) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rs = LBM_ECUDA;
+        msg = "set-up of the timing failed";
+    }
+    for (int c = 1; rs == LBM_OK && c <= b->occupancy; c++) {
+        b->ctas_per_sm = c;
+        float ms = 0.f;
+        // one untimed launch, then a timed one, each from the saved state
+        for (int rep = 0; rep < 2 && rs == LBM_OK; rep++) {
+            if (copy_state(false) != cudaSuccess) {
+                rs = LBM_ECUDA;
+                msg = "restore of the state failed";
+                break;
+            }
+            if (rep == 1 && cudaEventRecord(e0, b->stream) != cudaSuccess) rs = LBM_ECUDA;
+            if (rs == LBM_OK) rs = lbm_batch_launch(b, steps, 0);
+            if (rs == LBM_OK && rep == 1 && cudaEventRecord(e1, b->stream) != cudaSuccess) rs = LBM_ECUDA;
+            if (rs == LBM_OK) rs = lbm_batch_wait(b, nullptr);
+            if (rs != LBM_OK) msg = b->err.empty() ? "timing launch failed" : b->err;
+        }
+        if (rs == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rs = LBM_ECUDA;
+            msg = "event timing failed";
+        }
+        if (rs != LBM_OK) break;
+        const double per = (double)ms / steps;
+        if (ms_per_step) ms_per_step[c - 1] = per;
+        if (c == 1 || per < best_ms) {
+            best_ms = per;
+            best_c = c;
+        }
+    }
+    b->in_flight = false;
+    const cudaError_t er = copy_state(false);
+    const cudaError_t es = cudaStreamSynchronize(b->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(save, b->stream);
+    cudaStreamSynchronize(b->stream);
+    if (rs == LBM_OK && (er != cudaSuccess || es != cudaSuccess)) {
+        rs = LBM_ECUDA;
+        msg = "restore of the state failed";
+    }
+    b->ctas_per_sm = rs == LBM_OK ? best_c : (current == b->occupancy ? 0 : current);
+    if (rs != LBM_OK) return bfail(b, rs, "lbm_batch_autotune: " + msg);
+    if (best) *best = best_c;
     return LBM_OK;
 }
 

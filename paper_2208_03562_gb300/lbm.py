@@ -96,6 +96,9 @@ def load():
         "lbm_batch_remove": [B, C.c_int],
         "lbm_batch_set_stall": [B, C.c_int, C.c_long, C.c_double],
         "lbm_batch_set_wait_limit": [B, C.c_longlong, C.c_int],
+        "lbm_batch_set_ctas_per_sm": [B, C.c_int],
+        "lbm_batch_get_ctas_per_sm": [B, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "lbm_batch_autotune": [B, C.c_int, C.POINTER(C.c_int), _D],
         "lbm_batch_launch": [B, C.c_long, C.c_int],
         "lbm_batch_wait": [B, C.POINTER(C.c_int)],
         "lbm_batch_run": [B, C.c_long, C.POINTER(C.c_int)],
@@ -133,7 +136,8 @@ def exported_symbols():
                  "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
                  "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc", "lbm_batch_create",
                  "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_instance_bytes", "lbm_batch_add",
-                 "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_set_wait_limit", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
+                 "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_set_wait_limit",
+                 "lbm_batch_set_ctas_per_sm", "lbm_batch_get_ctas_per_sm", "lbm_batch_autotune", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
                  "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations",
                  "lbm_batch_mass", "lbm_batch_set_mass", "lbm_set_mass"):
         if hasattr(L, name):
@@ -485,6 +489,33 @@ class Batch:
         (0: the default) and, with hold, a withheld arrival that makes the
         waits run out (lbm_batch_set_wait_limit)."""
         _bcheck(load().lbm_batch_set_wait_limit(self.b, int(cycles), 1 if hold else 0), self.b)
+
+    @property
+    def ctas_per_sm(self) -> int:
+        """Resident CTAs per SM of the persistent grid (lbm_batch_get_ctas_per_sm)."""
+        c = C.c_int()
+        _bcheck(load().lbm_batch_get_ctas_per_sm(self.b, C.byref(c), None), self.b)
+        return c.value
+
+    @ctas_per_sm.setter
+    def ctas_per_sm(self, value: int):
+        _bcheck(load().lbm_batch_set_ctas_per_sm(self.b, int(value)), self.b)
+
+    @property
+    def max_ctas_per_sm(self) -> int:
+        m = C.c_int()
+        _bcheck(load().lbm_batch_get_ctas_per_sm(self.b, None, C.byref(m)), self.b)
+        return m.value
+
+    def autotune(self, steps: int = 20):
+        """Time every persistent-grid size on the active slots, restore their
+        state and keep the fastest (lbm_batch_autotune).  Returns (best
+        ctas_per_sm, milliseconds per step for ctas_per_sm = 1, 2, ...)."""
+        n = self.max_ctas_per_sm
+        best = C.c_int()
+        ms = (C.c_double * n)(*([-1.0] * n))
+        _bcheck(load().lbm_batch_autotune(self.b, int(steps), C.byref(best), ms), self.b)
+        return best.value, list(ms)
 
     def launch(self, steps: int, use_graph: bool = True):
         _bcheck(load().lbm_batch_launch(self.b, int(steps), 1 if use_graph else 0), self.b)

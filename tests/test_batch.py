@@ -193,3 +193,53 @@ def test_wait_limit_rejects_negative_cycles():
     with pytest.raises(L.LbmError) as e:
         b.set_wait_limit(-1)
     assert e.value.status == L.EINVAL
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F64])
+def test_launch_shape_leaves_results_and_autotune_restores_state(dtype):
+    """The persistent grid size changes how tiles are shared among CTAs, not
+    what any slot computes; lbm_batch_autotune puts every slot back."""
+    def make(cps):
+        b = L.Batch(8, dtype)
+        slots = []
+        for k, case in enumerate(MIX):
+            s = b.add(params(case, dtype), 0.0, 10 ** 6)
+            b.set_populations(s, start_state(case, 400 + k))
+            slots.append(s)
+        if cps:
+            b.ctas_per_sm = cps
+        return b, slots
+    a, sa = make(0)
+    one, s1 = make(1)
+    assert a.ctas_per_sm == a.max_ctas_per_sm >= 1 and one.ctas_per_sm == 1
+    a.run(33)
+    one.run(33)
+    for x, y in zip(sa, s1):
+        assert np.array_equal(a.populations(x), one.populations(y))
+    before = [(a.populations(x), a.query(x)[0].step) for x in sa]
+    best, ms = a.autotune(10)
+    assert 1 <= best <= a.max_ctas_per_sm and a.ctas_per_sm == best
+    assert len(ms) == a.max_ctas_per_sm and all(m > 0 for m in ms)
+    for x, (p, step) in zip(sa, before):
+        info, st = a.query(x)
+        assert st == L.SLOT_ACTIVE and info.step == step
+        assert np.array_equal(a.populations(x), p)
+    a.run(27)
+    one.run(27)
+    for x, y in zip(sa, s1):
+        assert np.array_equal(a.populations(x), one.populations(y))
+        assert a.query(x)[0].step == one.query(y)[0].step == 60
+
+
+def test_launch_shape_rejects_out_of_range():
+    b = L.Batch(2, L.F32)
+    m = b.max_ctas_per_sm
+    for bad in (-1, m + 1):
+        with pytest.raises(L.LbmError) as e:
+            b.ctas_per_sm = bad
+        assert e.value.status == L.EINVAL
+    b.ctas_per_sm = 1
+    b.ctas_per_sm = 0  # back to the default: the maximum
+    assert b.ctas_per_sm == m
+    best, ms = b.autotune(5)  # no active slot: nothing is timed
+    assert best == m and all(v == -1.0 for v in ms)
