@@ -243,3 +243,43 @@ def test_launch_shape_rejects_out_of_range():
     assert b.ctas_per_sm == m
     best, ms = b.autotune(5)  # no active slot: nothing is timed
     assert best == m and all(v == -1.0 for v in ms)
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F16])
+def test_specialised_kernel_equals_single_instances(dtype):
+    """A mix with the density-gradient terms, no force and the central scheme
+    everywhere runs the form of the batch kernel with the tile body fixed at
+    compile time.  Grids of several tiles in both directions, one with a
+    ragged last row and column of tiles and one smaller than a tile, must
+    give exactly what single handles on the general kernel give."""
+    cases = [  # nx, ny, r, gamma, nu, u_lid
+        (300, 100, 0.5, 0.3, 0.01, 0.03),
+        (200, 90, 2.0, 0.1, 0.01, 0.02),
+        (134, 26, 1.0, 0.6, 0.02, 0.05),
+        (70, 19, 1.0, 1.0, 0.02, 0.05),
+        (517, 211, 0.25, 0.2, 0.005, 0.02),
+    ]
+    b = L.Batch(len(cases), dtype)
+    slots, refs = [], []
+    for k, (nx, ny, r, gamma, nu, u) in enumerate(cases):
+        p = L.lbm_params_init(nx, ny, r, gamma, nu, u, dtype)
+        w = S.rest_weights(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u))
+        f0 = w[:, None, None] + I.noise(700 + k, (9, ny, nx), 1e-3)
+        s = b.add(p, 0.0, 10 ** 6)
+        b.set_populations(s, f0)
+        h = L.Lbm(p)
+        h.variant = -1
+        h.set_populations(f0)
+        slots.append(s)
+        refs.append(h)
+    for n in (1, 18, 41):  # crossing residual steps
+        b.run(n)
+        for s, h in zip(slots, refs):
+            h.step(n)
+            info, st = b.query(s)
+            assert st == L.SLOT_ACTIVE and info.step == h.info().step
+            assert np.array_equal(b.populations(s), h.populations())
+            if info.residual_step:
+                assert info.residual == h.residual() and info.mass == h.info().mass
+    for h in refs:
+        h.close()
