@@ -323,6 +323,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         I.tiles = I.tiles_x * ceil_div(sl.p.ny, prc::BY);
         I.tile_start = tiles;
         I.part_base = tiles;
+        I.t0 = b->h_dyn[i].t;
         I.drho = sl.p.drho == LBM_DRHO_CURRENT;
         I.force = sl.p.fx != 0.0 || sl.p.fy != 0.0;
         I.tol = sl.tol;

@@ -13,9 +13,13 @@
 // stalls: at the first residual evaluation at least `stall_window` steps after
 // the previous checkpoint, a residual above stall_ratio times the checkpoint's
 // retires the instance as STALLED (a precision floor: the rounding noise of the
-// storage format keeps the residual from falling further).  Its tiles are
-// skipped from the next step on.  The grid barrier is a bounded spin: when it
-// runs out it records LBM_ETIMEOUT and every CTA leaves.
+// storage format keeps the residual from falling further).  Its result is the
+// set of the step at which it retired; its tiles are skipped from the next
+// step on, or from the one after (the next step's tiles may start before the
+// bookkeeping that retires it ends; see k_batch), and that one extra step
+// writes only the other set.  One grid barrier per step separates the tiles
+// from the bookkeeping; it is a bounded spin: when it runs out it records
+// LBM_ETIMEOUT and every CTA leaves.
 #pragma once
 
 #include <type_traits>
@@ -56,6 +60,7 @@ struct BatchInst {
     int tiles_x, tiles;  // BX x BY tiling of the grid
     int tile_start;      // first global tile index of this instance in the launch
     int part_base;       // first partial-sum slot
+    long long t0;        // completed steps at the start of the launch
     int drho, force;
     double tol;
     long long max_steps;
@@ -229,9 +234,10 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
             const BatchInst &I = inst[i];
             if (i != ci) {
                 ci = i;
-                const BatchDyn *D = dyn + I.slot;
-                active = ld_relaxed_i32(&D->state) == BATCH_ACTIVE;
-                t = __ldcg(&D->t);
+                // an active instance has completed t0 + s steps; its state may
+                // be changing right now (see the bookkeeping below)
+                t = I.t0 + s;
+                active = ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && t < I.max_steps;
             }
             if (!active) continue;
             const bool epi = ((t + 1) % 20) == 0;
@@ -301,7 +307,17 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
                 if (D->state == BATCH_ACTIVE && t >= I.max_steps) D->state = BATCH_MAXSTEPS;
             }
         }
-        if (!grid_barrier(ctl)) return;
+        // No grid barrier here: the next step's tiles start while the
+        // bookkeeping of this one may still run.  Each instance's bookkeeping
+        // is done by one CTA, which alone writes its counter and state; the
+        // tiles take the step count from t0.  A tile that reads the state just
+        // before the instance is retired advances it once more: retirement by
+        // the residual (converged, diverged, stalled) happens at a residual
+        // step, so that extra step is not one (no snapshot or partial-sum
+        // writes), and it reads the instance's final set and writes only the
+        // other one.  The step limit is checked in the tiles themselves.  The
+        // partial sums that this bookkeeping reads are written again only 20
+        // steps later.
     }
 }
 
