@@ -283,3 +283,32 @@ def test_specialised_kernel_equals_single_instances(dtype):
                 assert info.residual == h.residual() and info.mass == h.info().mass
     for h in refs:
         h.close()
+
+
+def test_autotune_restores_state_when_a_wait_runs_out():
+    """A grid-barrier timeout during the timing launches ends lbm_batch_autotune
+    with LBM_ETIMEOUT after the slots' state is put back; the batch stays
+    usable and its launch shape unchanged."""
+    cases = [(64, 32, 1.0, 0.5, 0.02, 0.05), (200, 90, 2.0, 0.1, 0.01, 0.02)]
+    b = L.Batch(2, L.F32)
+    slots = []
+    for k, (nx, ny, r, gamma, nu, u) in enumerate(cases):
+        s = b.add(L.lbm_params_init(nx, ny, r, gamma, nu, u, L.F32), 0.0, 10 ** 6)
+        w = S.rest_weights(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u))
+        b.set_populations(s, w[:, None, None] + I.noise(900 + k, (9, ny, nx), 1e-3))
+        slots.append(s)
+    b.run(13)
+    before = [(b.populations(s), b.query(s)[0].step) for s in slots]
+    shape = b.ctas_per_sm
+    b.set_wait_limit(2_000_000, hold=True)  # the first timing launch's waits run out
+    with pytest.raises(L.LbmError) as e:
+        b.autotune(10)
+    assert e.value.status == L.ETIMEOUT
+    assert b.ctas_per_sm == shape
+    for s, (p, step) in zip(slots, before):
+        info, st = b.query(s)
+        assert st == L.SLOT_ACTIVE and info.step == step
+        assert np.array_equal(b.populations(s), p)
+    assert b.run(7) == 2
+    for s, (_, step) in zip(slots, before):
+        assert b.query(s)[0].step == step + 7
