@@ -218,13 +218,15 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
     const T R2s = vsub(n2s, nebr), R2d = vsub(n2d, nesr);
     // The two unknowns X, Y of the strain-rate system (Eqs. 43-44) solve
     //   (Cb0 rho + a_x) X + (Cb0 rho + a_y) Y = R2s,
-    //   (Cs0 rho + d_x) X + (d_y' - Cs0 rho) Y = R2d,
-    // with a_x = rho (k3x + P u_x^2 / 2 + Q u_y^2 / 2) and the like.  The
-    // system is homogeneous in rho, and the moments below use X and Y only as
-    // Xs = rho (X + Y) and Xd = rho (X - Y): by the two rows, the corrections
-    // a_x X + a_y Y + e_b and d_x X + d_y' Y + e_s are n2s - Cb0 Xs and
-    // n2d - Cs0 Xd.  So the system is solved for (Xs, Xd) directly, with
-    // rho = 1 and its coefficients taken half:
+    //   (Cs0 rho + d_x) X + (n_y - Cs0 rho) Y = R2d,
+    // with (P = P_gamma, Q = Q_gamma)
+    //   a_x = rho (k3x + P u_x^2 / 2 + Q u_y^2 / 2),  a_y = rho (k3y + P u_y^2 / 2 + Q u_x^2 / 2),
+    //   d_x = rho (k3x + P u_x^2 / 2 - Q u_y^2 / 2),  n_y = -rho (k3y + P u_y^2 / 2 - Q u_x^2 / 2).
+    // The system is homogeneous in rho, and the moments below use X and Y
+    // only as Xs = rho (X + Y) and Xd = rho (X - Y): by the two rows, the
+    // corrections c_s = a_x X + a_y Y + nebr and c_d = d_x X + n_y Y + nesr
+    // equal n2s - Cb0 Xs and n2d - Cs0 Xd.  So the system is solved for
+    // (Xs, Xd) directly, with rho = 1 and its coefficients taken half:
     //   m11 = Cb0 + (k3x + k3y)/2 + (P + Q)/4 (u_x^2 + u_y^2),
     //   m12 = (k3x - k3y)/2 + (P - Q)/4 (u_x^2 - u_y^2),
     //   m21 = (k3x - k3y)/2 + (P + Q)/4 (u_x^2 - u_y^2),
