@@ -247,8 +247,9 @@ lbm_status lbm_load(lbm_t h, const void *host_buf, size_t n);
  * restores the populations, the residual snapshot, the status and the step
  * counter exactly, selects the fastest and returns it in *best;
  * ms_per_step[0..n) receives the milliseconds per step of the interior
- * variants and ms_per_step[n] that of the cluster engine (-1 when it does
- * not fit), so the array holds n + 1 values.  Either pointer may be NULL.
+ * variants, ms_per_step[n] that of the cluster engine (-1 when it does not
+ * fit) and ms_per_step[n + 1] that of the general kernel, so the array holds
+ * n + 2 values.  Either pointer may be NULL.
  * No counterpart in the paper: these choose how the same update is executed.
  */
 #define LBM_VARIANT_CLUSTER (-2)
@@ -276,8 +277,9 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step);
  *   snap      ny x pitch values of u_x from the previous residual evaluation
  *             (double for LBM_F64, float otherwise); read and overwritten
  *             with the new u_x when with_residual != 0, untouched otherwise;
- *   out       when with_residual != 0: out[0] = ||u_x - snap||_2 (Sec. 5.2
- *             residual) and out[1] = sum of rho over the grid, both FP64.
+ *   out       when with_residual != 0: out[0] = the L2 norm of u_x minus
+ *             snap over the grid and out[1] = sum of rho over the grid, both
+ *             FP64.
  * The step is enqueued on `stream` (cudaStream_t, NULL = legacy default) and
  * runs the general wall-aware kernel on every node.
  *
@@ -289,9 +291,13 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step);
  * status word itself.  Calls whose kernels overlap on the GPU (different
  * streams, or different host threads) race on the scratch: serialise them.
  * The first call on each device looks up the scratch's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture.  The call itself performs no cudaMalloc,
- * cudaFree or allocating library call.
+ * (cudaGetSymbolAddress with that device current) and keeps it for the rest
+ * of the process; make that first call before any stream capture.  A device
+ * reset (cudaDeviceReset) ends the context that address belongs to: after
+ * one, do not call this entry point again in the same process.  The call
+ * itself performs no cudaMalloc, cudaFree or allocating library call.
+ * Arguments are checked before anything is enqueued: a null src, dst or
+ * snap, src == dst, or with_residual without out return LBM_EINVAL.
  */
 lbm_status lbm_step_noalloc(const lbm_params *p, const void *src, void *dst, void *snap, int with_residual,
                             double *out, void *stream);

@@ -870,10 +870,6 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
     const bool cluster_ok = cluster_select(h, cg) == LBM_OK;
     h->err.clear();
     if (ms_per_step) ms_per_step[nv] = -1.0;
-    if (nv == 0 && !cluster_ok) {
-        if (best) *best = -1;
-        return apply_variant(h, -1);
-    }
     CK(h, cudaStreamSynchronize(h->stream));
     // keep the state: copy the current populations, snapshot and status aside
     const long long t_keep = h->t;
@@ -893,9 +889,11 @@ lbm_status lbm_autotune(lbm_t h, int steps, int *best, double *ms_per_step)
     int arg = entry_variant;
     double bestms = 1e300;
     lbm_status rs = LBM_OK;
-    // candidates: the interior variants 0 .. nv-1, then the cluster engine
-    for (int v = 0; v < nv + (cluster_ok ? 1 : 0) && rs == LBM_OK; v++) {
-        const int var = v < nv ? v : LBM_VARIANT_CLUSTER;
+    // candidates: the interior variants 0 .. nv-1, the cluster engine (when
+    // the grid fits it), the general kernel
+    for (int v = 0; v < nv + 2 && rs == LBM_OK; v++) {
+        const int var = v < nv ? v : (v == nv ? LBM_VARIANT_CLUSTER : -1);
+        if (var == LBM_VARIANT_CLUSTER && !cluster_ok) continue;
         rs = apply_variant(h, var);
         if (rs != LBM_OK) break;
         // plain steps only: a step index of 0 or 1 (same buffer parity as t)
@@ -964,7 +962,9 @@ std::map<int, NoallocScratch> g_noalloc_addr;  // device ordinal -> device addre
 // Device addresses of the scratch arrays on the current device.  In host code
 // the array names are host-side stand-ins, not device addresses; the real
 // addresses come from cudaGetSymbolAddress with the device current, once per
-// device.
+// device.  They stay valid for the life of the device's primary context; a
+// device reset ends that context, and the entry point's contract excludes
+// calls after one.
 lbm_status noalloc_scratch(NoallocScratch *out)
 {
     int dev = -1;

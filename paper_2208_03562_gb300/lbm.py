@@ -301,12 +301,12 @@ def lbm_set_variant(h, variant):
 def lbm_autotune(h, dtype, steps=20):
     """Time every candidate on the handle's grid; selects the fastest.
     Returns (best, [ms per step of each interior variant, then of the
-    cluster engine (-1 when it does not fit)])."""
+    cluster engine (-1 when it does not fit), then of the general kernel])."""
     n = lbm_variant_count(dtype)
-    ms = (C.c_double * (n + 1))()
+    ms = (C.c_double * (n + 2))()
     best = C.c_int()
     _check(load().lbm_autotune(h, int(steps), C.byref(best), ms), h)
-    return best.value, [ms[i] for i in range(n + 1)]
+    return best.value, [ms[i] for i in range(n + 2)]
 
 
 def lbm_step_noalloc(p: lbm_params, src_ptr: int, dst_ptr: int, snap_ptr: int, with_residual: bool,

@@ -105,7 +105,8 @@ def test_cluster_autotune_restores_state():
     h.step(33)
     before = h.populations()
     best, ms = h.autotune(20)
-    assert len(ms) == L.lbm_variant_count(L.F32) + 1 and ms[-1] > 0
+    nv = L.lbm_variant_count(L.F32)
+    assert len(ms) == nv + 2 and ms[nv] > 0 and ms[nv + 1] > 0
     assert np.array_equal(h.populations(), before) and h.info().step == 33
 
 

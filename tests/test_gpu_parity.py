@@ -207,8 +207,11 @@ def test_autotune_restores_state_exactly():
     before = g.populations()
     info = g.info()
     best, ms = g.autotune(10)
-    # interior variants, then the cluster engine (-1: this grid does not fit it)
-    assert 0 <= best < len(ms) - 1 and all(m > 0 for m in ms[:-1]) and ms[-1] == -1.0
+    # interior variants, the cluster engine (-1: this grid does not fit it),
+    # the general kernel
+    nv = L.lbm_variant_count(L.F32)
+    assert len(ms) == nv + 2 and ms[nv] == -1.0 and all(m > 0 for m in ms[:nv] + ms[nv + 1:])
+    assert best == -1 or 0 <= best < nv
     assert g.variant == best
     assert np.array_equal(before, g.populations())
     assert g.info().step == info.step and g.info().residual == info.residual
