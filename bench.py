@@ -194,25 +194,44 @@ def gpu_leg(cav_dtype, steps, warmup, torch, L, dist=None, clocks_index=None):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(clocks_index) if clocks_index is not None else None
     if sampler:
         sampler.__enter__()
         time.sleep(0.4)
-    t0.record(stream)
-    g.step(steps)
-    t1.record(stream)
-    torch.cuda.synchronize()
+    regions = timed_regions(g, steps, stream, torch, dist)
     if sampler:
         sampler.__exit__()
-    ms = t0.elapsed_time(t1)
-    if dist:
-        ms = max_over_ranks(ms, dist, torch, "cuda")
-        dist.barrier()
+    ms = sorted(regions)[len(regions) // 2]
     info = g.info()
     launch = launch_times(g, min(steps, 200), torch)
     g.close()
+    tuned["regions_ms"] = {"n": len(regions), "median": ms, "min": min(regions), "max": max(regions)}
     return cav, ms, info, (sampler.summary() if sampler else None), tuned, launch
+
+
+def timed_regions(g, steps, stream, torch, dist, min_total_s=0.5, max_regions=200):
+    """Time regions of exactly `steps` steps, each bracketed by a barrier (under
+    torchrun) and a device synchronisation on both sides and timed with CUDA
+    events on the stream the step kernel is launched on, until at least
+    min_total_s of device time has been measured (at least three regions).
+    Every region is the max over ranks.  The caller reports the median."""
+    out, total = [], 0.0
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while len(out) < 3 or (total < min_total_s * 1e3 and len(out) < max_regions):
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0.record(stream)
+        g.step(steps)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        if dist:
+            ms = max_over_ranks(ms, dist, torch, "cuda")
+            dist.barrier()
+        out.append(ms)
+        total += ms
+    return out
 
 
 def max_over_ranks(value, dist, torch, device):
@@ -284,106 +303,329 @@ def e2e_leg(steps, torch, L):
                                   "bytes per step are the per-solve transfers divided by the steps" % steps}
 
 
-def ttss_leg(L, budget_s=60.0):
-    """Time to steady state on the deep cavity (128 x 128, r = 2, Re = 1000,
-    Ma = 0.06), to residual 1e-6 (Sec. 5.2), wall time from the first step to
-    the step that met the residual, with the residual checks included:
-    - the preconditioned FP32 path (gamma = 0.1), a single-instance handle,
-      also to residual 1e-7;
-    - the FP16 -> FP32 precision schedule (gamma = 0.1) through the solve
-      server (batch engine, stall test on the device) and on single-instance
-      handles (stall test on the host between launches);
-    - the plain FP64 path (gamma = 1, no preconditioning), for at most
-      budget_s seconds: on this grid it does not settle (its shear rate is
-      close to the stability limit), so the figure is a lower bound."""
+# ---------------------------------------------------------------------------
+# time to steady state, with the error of every result against the FP64 oracle
+
+def deep_cavity_100x150(gamma, dtype):
+    """The paper's deep cavity at Re = 1000 (Sec. 5.2): AR = 2 on 100 x 150
+    nodes, r = 4/3, Ma = 0.06, to residual 1e-6."""
     from paper_2208_03562_gb300 import inputs as I
-    import time as _t
-    out = {"workload": "deep lid-driven cavity 128x128, r=2 (H/L=2), Re=1000, Ma=0.06, from rest",
-           "tol": 1e-6}
-    for name, dt, gamma, bud, tol in (("f32_gamma0.1", L.F32, 0.1, budget_s / 3, 1e-6),
-                                      ("f32_gamma0.1_tol1e-7", L.F32, 0.1, budget_s / 3, 1e-7),
-                                      ("f16_to_f32_gamma0.1", None, 0.1, budget_s / 3, 1e-6),
-                                      ("f16_to_f32_gamma0.1_single", "single", 0.1, budget_s / 3, 1e-6),
-                                      ("f64_plain_gamma1", L.F64, 1.0, budget_s, 1e-6)):
-        cav = I.deep_cavity_128(gamma)
-        t0 = _t.perf_counter()
-        steps, st = 0, None
-        if dt == "single":  # the same schedule on single-instance handles (cluster engine)
-            from paper_2208_03562_gb300 import serve as SV
-            r = SV.solve_promoted(cav.nx, cav.ny, cav.r, gamma, cav.nu, cav.u_lid, 1e-6, 20_000_000)
-            out[name] = {"status": r["status"], "steps": r["steps"], "steps_by_stage": r["steps_by_stage"],
-                         "s": _t.perf_counter() - t0, "residual": r.get("residual")}
+    return I.Cavity(100, 150, 4.0 / 3.0, gamma, 1000.0, 0.06 * I.CS_STAR, dtype, 1e-6, 5_000_000)
+
+
+def oracle_solve(job):
+    """Runs in a spawned worker process: the FP64 oracle from rest to each
+    tolerance of `tols` in turn (blocks of 20 steps, Sec. 5.2 residual).
+    Returns {tol: (status, steps, residual, u_x, u_y, seconds)}."""
+    from oracle import stepper as S
+    cav, tols, max_steps, threads = job
+    S.num_threads(threads)
+    o = S.Oracle(S.OracleParams(nx=cav["nx"], ny=cav["ny"], r=cav["r"], gamma=cav["gamma"], nu=cav["nu"],
+                                u_lid=cav["u_lid"]))
+    out, done, t0 = {}, 0, time.perf_counter()
+    for tol in tols:
+        n, res = o.run(tol, max_steps - done)
+        done += n
+        _, ux, uy = o.fields()
+        st = "converged" if res < tol else ("diverged" if res != res or res == float("inf") else "maxsteps")
+        out[tol] = (st, done, res, ux, uy, time.perf_counter() - t0)
+        if st != "converged":
+            break
+    return out
+
+
+class OracleJobs:
+    """FP64 oracle runs on the host cores, in spawned worker processes, while
+    the GPU legs run; each GPU result is compared with its oracle result when
+    both are in."""
+
+    def __init__(self, jobs, workers=3):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        cores = len(os.sched_getaffinity(0))
+        self.threads = max(1, (cores - 4) // workers)
+        self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+        self.fut = {}
+        for name, cav, tols, max_steps in jobs:
+            d = {"nx": cav.nx, "ny": cav.ny, "r": cav.r, "gamma": cav.gamma, "nu": cav.nu, "u_lid": cav.u_lid}
+            self.fut[name] = self.ex.submit(oracle_solve, (d, tols, max_steps, self.threads))
+
+    def result(self, name, tol, timeout):
+        try:
+            return self.fut[name].result(timeout=timeout).get(tol)
+        except Exception:
+            return None
+
+    def close(self):
+        """Stop every worker (a run still going is abandoned), so that nothing
+        else loads the host cores afterwards."""
+        for f in self.fut.values():
+            f.cancel()
+        procs = list(getattr(self.ex, "_processes", {}).values())
+        self.ex.shutdown(wait=False, cancel_futures=True)
+        for pr in procs:
+            if pr.is_alive():
+                pr.terminate()
+            pr.join(timeout=10)
+
+
+def rel_l2(a, b):
+    """||(u_x, u_y)_a - (u_x, u_y)_b||_2 / ||(u_x, u_y)_b||_2."""
+    import numpy as np
+    num = np.sum((a[0] - b[0]) ** 2 + (a[1] - b[1]) ** 2)
+    den = np.sum(b[0] ** 2 + b[1] ** 2)
+    return float(np.sqrt(num / den))
+
+
+PENDING = []
+
+
+def with_oracle(entry, fields, oj, name, tol, timeout):
+    """Queue the comparison of a GPU result with the FP64 oracle's run to the
+    same residual; resolve_oracle() adds the oracle's steps and the relative
+    L2 error of (u_x, u_y) once the oracle has finished."""
+    PENDING.append((entry, fields, oj, name, tol, timeout))
+    return entry
+
+
+def resolve_oracle():
+    t0 = time.perf_counter()
+    for entry, fields, oj, name, tol, timeout in PENDING:
+        r = oj.result(name, tol, max(1.0, timeout - (time.perf_counter() - t0))) if oj else None
+        if r is None:
+            entry["oracle"] = "unavailable (not finished within %.0f s)" % timeout
             continue
-        if dt is None:  # FP16 storage until the residual stalls, then FP32
-            from paper_2208_03562_gb300 import serve as SV
-            srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=2, reserve_bytes=0, budget_bytes=1 << 30,
-                                keep_fields=False)
-            p = L.lbm_params_init(cav.nx, cav.ny, cav.r, gamma, cav.nu, cav.u_lid, L.F16)
-            r = srv.serve([SV.SolveRequest(0, 0.0, p, 1e-6, 20_000_000)], time_limit_s=bud)
-            srv.close()
-            dts = _t.perf_counter() - t0
-            if r:
-                out[name] = {"status": r[0].status, "steps": r[0].steps, "steps_by_stage": r[0].steps_by_stage,
-                             "s": dts, "residual": r[0].residual}
-            else:
-                out[name] = {"status": "unfinished", "s": dts}
-            continue
-        p = L.lbm_params_init(cav.nx, cav.ny, cav.r, gamma, cav.nu, cav.u_lid, dt)
-        g = L.Lbm(p)
-        while _t.perf_counter() - t0 < bud:
-            st, n = g.run(tol, 100000)
-            steps += n
-            if st == L.OK:
-                break
-        dts = _t.perf_counter() - t0
-        out[name] = {"status": "converged" if st == L.OK else "unfinished", "steps": steps, "s": dts,
-                     "residual": g.residual(), "us_per_step": 1e6 * dts / max(steps, 1), "tol": tol}
-        g.close()
-    a, b = out.get("f32_gamma0.1", {}), out.get("f64_plain_gamma1", {})
-    if a.get("status") == "converged" and b.get("status") == "converged":
-        out["speedup_f32_vs_f64_plain"] = b["s"] / a["s"]
-        out["step_ratio_gamma1_over_gamma0.1"] = b["steps"] / a["steps"]
+        st, steps, res, ux, uy, secs = r
+        entry["oracle_steps"] = steps
+        entry["oracle_status"] = st
+        if fields is not None and st == "converged":
+            entry["oracle_rel_l2"] = rel_l2((fields[1], fields[2]), (ux, uy))
+    PENDING.clear()
+
+
+def gpu_solve(L, cav, dtype, tol, budget_s, tune=False):
+    """One steady-state solve from rest on a single-instance handle: wall time
+    from the first step to the launch that met the residual, residual checks
+    included.  With tune, the library's autotuner first picks the engine
+    (interior variants, cluster engine, general kernel; the state is restored
+    and the tuning is not in the time)."""
+    p = L.lbm_params_init(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, dtype)
+    g = L.Lbm(p)
+    tuned = g.autotune(200) if tune else None
+    t0 = time.perf_counter()
+    steps, st = 0, None
+    while time.perf_counter() - t0 < budget_s:
+        st, n = g.run(tol, 100000)
+        steps += n
+        if st == L.OK:
+            break
+    dts = time.perf_counter() - t0
+    out = {"status": "converged" if st == L.OK else "unfinished", "steps": steps, "s": dts,
+           "residual": g.residual(), "us_per_step": 1e6 * dts / max(steps, 1), "engine": g.variant}
+    if tuned:
+        out["autotune_ms_per_step"] = tuned[1]
+    fields = g.fields() if st == L.OK else None
+    g.close()
+    return out, fields
+
+
+def promoted_solve(cav, tol):
+    """The FP16 -> FP32 precision schedule on single-instance handles."""
+    from paper_2208_03562_gb300 import serve as SV
+    t0 = time.perf_counter()
+    r = SV.solve_promoted(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, tol, 20_000_000)
+    out = {"status": r["status"], "steps": r["steps"], "steps_by_stage": r["steps_by_stage"],
+           "s": time.perf_counter() - t0, "residual": r.get("residual")}
+    return out, r.get("fields")
+
+
+def ttss_leg(L, oj, c2_f64_budget_s=20.0, budget_s=30.0):
+    """Time to steady state (Sec. 5.2), each result with its error against the
+    FP64 oracle run from rest to the same residual:
+    - deep cavity 100 x 150 (AR = 2, r = 4/3, Re = 1000, Ma = 0.06), residual
+      1e-6: the plain FP64 path at gamma = 1 against the preconditioned FP32
+      path (gamma = 0.1) and the FP16 -> FP32 schedule (gamma = 0.1), with the
+      step and time ratios;
+    - deep cavity 128 x 128 (r = 2, Re = 1000, Ma = 0.06): FP32 gamma = 0.1 to
+      1e-6 and to 1e-7, the FP16 -> FP32 schedule on the batch engine (the
+      solve server) and on single-instance handles, and the plain FP64 gamma = 1
+      path for at most c2_f64_budget_s seconds (it does not settle on this
+      grid: a lower bound);
+    - the square cavity 64 x 64 (r = gamma = 1, Re = 100, U = 0.1) in FP64 to
+      1e-8."""
+    from paper_2208_03562_gb300 import inputs as I
+    from paper_2208_03562_gb300 import serve as SV
+    out = {}
+    # deep cavity 100 x 150
+    d = {"workload": "deep lid-driven cavity 100x150, AR=2, r=4/3, Re=1000, Ma=0.06, from rest (Sec. 5.2)",
+         "tol": 1e-6}
+    c1 = deep_cavity_100x150(1.0, "f64")
+    r, f = gpu_solve(L, c1, L.F64, 1e-6, 4 * budget_s, tune=True)
+    d["f64_plain_gamma1"] = with_oracle(r, f, oj, "deep100_g1", 1e-6, 240)
+    c01 = deep_cavity_100x150(0.1, "f32")
+    r, f = gpu_solve(L, c01, L.F32, 1e-6, budget_s)
+    d["f32_gamma0.1"] = with_oracle(r, f, oj, "deep100_g0.1", 1e-6, 120)
+    r, f = gpu_solve(L, deep_cavity_100x150(1.0, "f32"), L.F32, 1e-6, budget_s)
+    d["f32_gamma1"] = with_oracle(r, f, oj, "deep100_g1", 1e-6, 240)
+    r, f = promoted_solve(c01, 1e-6)
+    d["f16_to_f32_gamma0.1"] = with_oracle(r, f, oj, "deep100_g0.1", 1e-6, 120)
+    a, b, c = d["f32_gamma0.1"], d["f64_plain_gamma1"], d["f16_to_f32_gamma0.1"]
+    if a["status"] == "converged" and b["status"] == "converged":
+        d["speedup_f32_vs_f64_plain"] = b["s"] / a["s"]
+        d["step_ratio_f64_gamma1_over_f32_gamma0.1"] = b["steps"] / a["steps"]
+    if c["status"] == "converged" and b["status"] == "converged":
+        d["speedup_f16_to_f32_vs_f64_plain"] = b["s"] / c["s"]
+    out["deep_100x150"] = d
+    # deep cavity 128 x 128
+    e = {"workload": "deep lid-driven cavity 128x128, r=2 (H/L=2), Re=1000, Ma=0.06, from rest", "tol": 1e-6}
+    cav = I.deep_cavity_128(0.1)
+    r, f = gpu_solve(L, cav, L.F32, 1e-6, budget_s)
+    e["f32_gamma0.1"] = with_oracle(r, f, oj, "deep128_g0.1", 1e-6, 120)
+    r, f = gpu_solve(L, cav, L.F32, 1e-7, budget_s)
+    e["f32_gamma0.1_tol1e-7"] = with_oracle(r, f, oj, "deep128_g0.1", 1e-7, 120)
+    t0 = time.perf_counter()
+    srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=2, reserve_bytes=0, budget_bytes=1 << 30,
+                        keep_fields=True)
+    p = L.lbm_params_init(cav.nx, cav.ny, cav.r, cav.gamma, cav.nu, cav.u_lid, L.F16)
+    res = srv.serve([SV.SolveRequest(0, 0.0, p, 1e-6, 20_000_000)], time_limit_s=budget_s)
+    srv.close()
+    if res:
+        r = {"status": res[0].status, "steps": res[0].steps, "steps_by_stage": res[0].steps_by_stage,
+             "s": time.perf_counter() - t0, "residual": res[0].residual, "engine": "batch"}
+        e["f16_to_f32_gamma0.1"] = with_oracle(r, res[0].fields, oj, "deep128_g0.1", 1e-6, 120)
+    r, f = promoted_solve(cav, 1e-6)
+    e["f16_to_f32_gamma0.1_single"] = with_oracle(r, f, oj, "deep128_g0.1", 1e-6, 120)
+    c64 = I.deep_cavity_128(1.0, "f64")
+    r, _ = gpu_solve(L, c64, L.F64, 1e-6, c2_f64_budget_s, tune=True)
+    r["note"] = "lower bound: stopped at the time budget (omega_nu = 1.90 at gamma = 1; no oracle run)"
+    e["f64_plain_gamma1"] = r
+    out["deep_128x128"] = e
+    # square cavity 64 x 64, FP64
+    q = I.square_cavity_64()
+    r, f = gpu_solve(L, q, L.F64, 1e-8, budget_s, tune=True)
+    out["square_64x64_f64"] = with_oracle(r, f, oj, "square64", 1e-8, 60)
+    out["square_64x64_f64"]["workload"] = "square cavity 64x64, r=gamma=1, Re=100, U=0.1, FP64, residual 1e-8"
+    return out
+
+
+def ttss_oracle_jobs():
+    """The FP64 oracle runs that the time-to-steady-state results are
+    compared with (name, cavity, tolerances, step limit)."""
+    from paper_2208_03562_gb300 import inputs as I
+    return [("deep100_g1", deep_cavity_100x150(1.0, "f64"), [1e-6], 2_000_000),
+            ("deep128_g0.1", I.deep_cavity_128(0.1, "f64"), [1e-6, 1e-7], 2_000_000),
+            ("deep100_g0.1", deep_cavity_100x150(0.1, "f64"), [1e-6], 2_000_000),
+            ("square64", I.square_cavity_64(), [1e-8], 20000)]
+
+
+def run_batch(L, cavs, budget_s):
+    """One batch of the given cavities (FP32), persistent launches of 2000
+    steps until every slot retired or the time budget ran out.  Returns
+    per-cavity (state, steps, residual, projected remaining steps or None)
+    and the launch record."""
+    import math
+    b = L.Batch(max(1, len(cavs)), L.F32)
+    slots = []
+    for c in cavs:
+        p = L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
+        slots.append((b.add(p, c.tol, c.max_steps), c))
+    best, ms = b.autotune(20) if cavs else (None, [])  # persistent-grid size; slot state restored
+    t0 = time.perf_counter()
+    launches, active = 0, len(cavs)
+    hist = {s: [] for s, _ in slots}
+    while active and time.perf_counter() - t0 < budget_s:
+        active = b.run(2000)
+        launches += 1
+        for s, _ in slots:
+            info, st = b.query(s)
+            if st == L.SLOT_ACTIVE:
+                hist[s] = (hist[s] + [(info.step, info.residual)])[-4:]
+    dt = time.perf_counter() - t0
+    per = []
+    for s, c in slots:
+        info, st = b.query(s)
+        left = None
+        if st == L.SLOT_ACTIVE:
+            h = hist[s]
+            if len(h) >= 2 and 0 < h[-1][1] < h[0][1]:
+                rate = math.log(h[0][1] / h[-1][1]) / (h[-1][0] - h[0][0])
+                left = max(0.0, min(math.log(h[-1][1] / c.tol) / rate, c.max_steps - info.step))
+        per.append((L.SLOT_NAMES[st], int(info.step), float(info.residual), left))
+    b.close()
+    return per, {"wall_s": dt, "launches": launches, "autotune": {"ctas_per_sm": best, "ms_per_step": ms}}
+
+
+def batch_summary(cavs, per, wall_s):
+    n = len(cavs)
+    ns = sum(step * c.nodes for (_, step, _, _), c in zip(per, cavs))
+    states = {}
+    for st, _, _, _ in per:
+        states[st] = states.get(st, 0) + 1
+    agg = ns / wall_s / 1e9
+    out = {"workload": "%d cavities, nx 64..1024, ny 32..512, r in {0.25,0.5,1,2}, gamma 0.05..1, Re 100..5000, "
+                       "FP32, residual 1e-7 (seed 0)" % n,
+           "aggregate_glups": agg, "wall_s": wall_s, "states": states,
+           "retired_fraction": (n - states.get("ACTIVE", 0)) / n}
+    if states.get("ACTIVE", 0):
+        rem = sum(left * c.nodes for (st, _, _, left), c in zip(per, cavs) if st == "ACTIVE" and left is not None)
+        stuck = sum(1 for st, _, _, left in per if st == "ACTIVE" and left is None)
+        out["projected_wall_s_to_retire_all"] = wall_s + rem / (agg * 1e9)
+        out["projection"] = ("active slots: remaining steps from the residual decay over their last launches "
+                             "(capped at the step limit), remaining node-steps at the measured aggregate rate; "
+                             "%d active slots whose residual did not fall are not in it" % stuck)
     return out
 
 
 def batch_leg(L, budget_s=30.0, n=256):
     """The batched sweep: n uneven cavities (seed 0) in one batch, persistent
     launches until every slot retired or the time budget ran out; aggregate
-    GLUPS over the slots' own steps."""
+    GLUPS over the slots' own steps, the fraction retired, and a projection of
+    the wall time to retire the whole mix: each active slot's remaining steps
+    from the decay of its residual over the last launches, and the remaining
+    node-steps at the measured aggregate rate."""
     from paper_2208_03562_gb300 import inputs as I
-    import time as _t
     cavs = I.batched_sweep(seed=0, n=n, dtype="f32")
-    b = L.Batch(n, L.F32)
-    slots = []
-    for c in cavs:
-        p = L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
-        slots.append((b.add(p, c.tol, c.max_steps), c.nodes))
-    best, ms = b.autotune(20)  # persistent-grid size; the slots' state is restored
-    t0 = _t.perf_counter()
-    launches, active = 0, n
-    while active and _t.perf_counter() - t0 < budget_s:
-        active = b.run(2000)
-        launches += 1
-    dt = _t.perf_counter() - t0
-    ns, states = 0, {}
-    for s, nodes in slots:
-        info, st = b.query(s)
-        ns += info.step * nodes
-        states[L.SLOT_NAMES[st]] = states.get(L.SLOT_NAMES[st], 0) + 1
-    b.close()
-    return {"workload": "%d cavities, nx 64..1024, ny 32..512, r in {0.25,0.5,1,2}, gamma 0.05..1, Re 100..5000, "
-                        "FP32, residual 1e-7 (seed 0)" % n,
-            "aggregate_glups": ns / dt / 1e9, "wall_s": dt, "launches": launches, "states": states,
-            "autotune": {"ctas_per_sm": best, "ms_per_step": ms},
-            "note": "time-bounded: slots still ACTIVE had not reached 1e-7 when the budget ran out"}
+    per, rec = run_batch(L, cavs, budget_s)
+    out = batch_summary(cavs, per, rec["wall_s"])
+    out["launches"] = rec["launches"]
+    out["autotune"] = rec["autotune"]
+    return out
 
 
-def serve_leg(L, budget_s=60.0, n=64, scale=4):
+def batch_leg_sharded(L, dist, rank, world, torch, budget_s=30.0, n=256):
+    """The batched sweep on `world` GPUs: whole cavities placed on ranks by
+    the greedy bytes x expected-steps balance (shard.py), one batch per rank,
+    no collective on the data path; per-cavity results gathered on rank 0.
+    The wall time is the slowest rank's."""
+    from paper_2208_03562_gb300 import inputs as I
+    from paper_2208_03562_gb300 import shard as SH
+    cavs = I.batched_sweep(seed=0, n=n, dtype="f32")
+    rec = {}
+
+    def solve(mine):
+        per, r = run_batch(L, mine, budget_s)
+        rec.update(r)
+        return per
+
+    torch.cuda.synchronize()
+    dist.barrier()
+    per = SH.run_sharded(cavs, [SH.cost(c) for c in cavs], solve, rank, world, dist)
+    wall = max_over_ranks(rec["wall_s"], dist, torch, "cuda")
+    if rank != 0:
+        return None
+    out = batch_summary(cavs, per, wall)
+    out["placement"] = "greedy longest-first over bytes x expected steps, %d ranks" % world
+    return out
+
+
+def serve_leg(L, budget_s=60.0, n=256, scale=1, capacity=16):
     """The serving workload: Poisson arrivals (50/s, seed 0) of steady-state
-    solves, FP16 storage until the residual stalls, then FP32 to 1e-6. The
-    bench runs the first n requests with both grid dimensions divided by
-    `scale`. The full mix (256 requests up to 2048 x 1024, ~1e5-1e6 steps
-    each) takes tens of GPU-minutes."""
+    solves, FP16 storage until the residual stalls, then FP32 to 1e-6, for at
+    most budget_s seconds; the requests still running or waiting then are
+    counted as unfinished.  At most `capacity` solves share the device at a
+    time (first come, first served, and within device memory): the offered
+    load is far above what the device completes, and with every request
+    admitted at once none would finish within the budget."""
     from paper_2208_03562_gb300 import inputs as I
     from paper_2208_03562_gb300 import serve as SV
     reqs = []
@@ -391,14 +633,16 @@ def serve_leg(L, budget_s=60.0, n=64, scale=4):
         c = rq.cavity
         reqs.append(SV.SolveRequest(i, rq.arrival_s, L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid,
                                                                         L.F16), c.tol, c.max_steps))
-    srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=n, keep_fields=False)
+    srv = SV.gpu_server(SV.fp16_schedule(2000), capacity=capacity, keep_fields=False)
     res = srv.serve(reqs, time_limit_s=budget_s)
     sm = SV.summary(srv, res)
     srv.close()
     sm["unfinished"] = n - len(res)
-    sm["workload"] = ("first %d requests of the serving mix (Poisson 50/s, nx 128..2048, ny 64..1024, r 0.25..2, "
-                      "gamma 0.05..1, Re 100..1000, seed 0) with both grid dimensions divided by %d; "
-                      "FP16->FP32, residual 1e-6" % (n, scale))
+    sm["workload"] = ("%d requests of the serving mix (Poisson 50/s, nx 128..2048, ny 64..1024, r 0.25..2, "
+                      "gamma 0.05..1, Re 100..1000, seed 0)%s; FP16->FP32, residual 1e-6, %.0f s budget, "
+                      "at most %d solves on the device at a time"
+                      % (n, "" if scale == 1 else " with both grid dimensions divided by %d" % scale, budget_s,
+                         capacity))
     sm["note"] = "time-bounded: percentiles are over the requests that finished within the budget"
     return sm
 
@@ -524,37 +768,52 @@ def main():
             "clocks": clocks,
             "residual_at_end": info.residual,
             "autotune": tuned}
+    extras = {}
     if not args.no_extras and args.dtype == "f32":
         cav16, ms16, _, _, tuned16, launch16 = gpu_leg("f16", args.steps, args.warmup, torch, L, dist, None)
         s16 = ms16 / args.steps
         a16 = BYTES_PER_NODE["f16"] * nodes / (s16 / 1e3) / 1e9
-        line["fp16"] = {"value": world * nodes * args.steps / (ms16 / 1e3) / 1e9, "unit": "GLUPS",
-                        "ms_per_step": s16, "roofline": {"achieved": a16, "peak": peak, "frac": a16 / peak,
-                                                         "bytes_per_node": 36,
-                                                         "traffic": ncu_traffic("k_step_f16"),
-                                                         "timing": kernel_timing(s16, launch16)},
-                        "autotune": tuned16}
-    if not args.no_extras and args.dtype == "f32":
-        cav64, ms64, _, _, _, launch64 = gpu_leg("f64", max(20, args.steps // 10), args.warmup, torch, L, dist, None)
+        extras["fp16"] = {"value": world * nodes * args.steps / (ms16 / 1e3) / 1e9, "unit": "GLUPS",
+                          "ms_per_step": s16,
+                          "roofline": {"bound": "hbm", "achieved": a16, "peak": peak, "unit": "GB/s",
+                                       "frac": a16 / peak, "bytes_per_node": 36,
+                                       "traffic": ncu_traffic("k_step_f16")},
+                          "variant": tuned16.get("variant"), "regions_ms": tuned16.get("regions_ms"),
+                          "what": "FP16 shifted storage, FP32 collision, same workload and timing"}
+        cav64, ms64, _, _, _, launch64 = gpu_leg("f64", max(20, args.steps // 10), args.warmup, torch, L, dist,
+                                                 None)
         st64 = max(20, args.steps // 10)
-        line["fp64"] = {"value": world * nodes * st64 / (ms64 / 1e3) / 1e9, "unit": "GLUPS",
-                        "ms_per_step": ms64 / st64, "steps": st64,
-                        "roofline_hbm": {"achieved": 144 * nodes / (ms64 / st64 / 1e3) / 1e9,
-                                         "peak": peak, "bytes_per_node": 144,
-                                         "timing": kernel_timing(ms64 / st64, launch64)},
-                        "note": "plain FP64 path (general kernel, FP64 collision): bound by FP64 ALU throughput"}
+        extras["fp64"] = {"value": world * nodes * st64 / (ms64 / 1e3) / 1e9, "unit": "GLUPS",
+                          "ms_per_step": ms64 / st64, "steps": st64,
+                          "hbm_frac": 144 * nodes / (ms64 / st64 / 1e3) / 1e9 / peak,
+                          "what": "plain FP64 path (general kernel, FP64 collision): bound by FP64 ALU throughput"}
+    if world > 1 and not args.no_extras and "batched_sweep" not in args.skip:
+        try:
+            r = batch_leg_sharded(L, dist, rank, world, torch)
+        except Exception as e:  # reported, not hidden
+            r = {"error": repr(e)}
+        if rank == 0:
+            extras["batched_sweep"] = r
     if rank == 0 and not args.no_extras:
         try:
             line["e2e"] = e2e_leg(args.steps, torch, L)
         except Exception as e:  # reported, not hidden
             line["e2e"] = {"error": repr(e)}
-        for key, fn in (("time_to_steady_state", ttss_leg), ("batched_sweep", batch_leg), ("serving", serve_leg)):
-            if key in args.skip:
+        oj = None
+        if "time_to_steady_state" not in args.skip:
+            oj = OracleJobs(ttss_oracle_jobs())
+        for key, fn in (("time_to_steady_state", lambda L: ttss_leg(L, oj)), ("batched_sweep", batch_leg),
+                        ("serving", serve_leg)):
+            if key in args.skip or key in extras:
                 continue
             try:
-                line[key] = fn(L)
+                extras[key] = fn(L)
             except Exception as e:  # reported, not hidden
-                line[key] = {"error": repr(e)}
+                extras[key] = {"error": repr(e)}
+        if oj:
+            resolve_oracle()
+            extras["time_to_steady_state"]["oracle_cores"] = {"workers": 3, "threads_each": oj.threads}
+            oj.close()
         v1, _, steps1, dt1 = oracle_sample_rate(8192, 8, steps_budget_s=3.0, max_steps=100, threads=1)
         v, threads, steps, dt = oracle_sample_rate(8192, 64)
         line["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": threads, "kind": "oracle",
@@ -563,6 +822,10 @@ def main():
                                 "single_core": {"value": v1, "unit": "GLUPS", "cores": 1,
                                                 "sample": "FP64 oracle on an 8192x8 slab, %d steps, %.1f s"
                                                           % (steps1, dt1)}}
+    # the large objects first, the compact FP64 / FP16 summaries last
+    for key in ("time_to_steady_state", "batched_sweep", "serving", "fp64", "fp16"):
+        if key in extras:
+            line[key] = extras[key]
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -38,6 +38,20 @@ def random_fields(seed: int, nx: int, ny: int, drho: float = 1e-2, u: float = 0.
     return rho, ux, uy
 
 
+def sample_nodes(seed: int, k: int, nx: int, ny: int) -> np.ndarray:
+    """k distinct flat node indexes (y * nx + x) drawn without replacement."""
+    return np.sort(rng(seed).choice(nx * ny, size=min(k, nx * ny), replace=False))
+
+
+def projection_signs(seed: int, k: int, nx: int, ny: int) -> np.ndarray:
+    """k random +-1 fields of shape (k, 2, ny, nx): weights of k random
+    projections of a velocity field (u_x, u_y).  For a difference field d,
+    the mean of (sum w d)^2 over the projections is an unbiased estimate of
+    ||d||_2^2, so a few stored projections let a test estimate the L2
+    distance to a field it does not hold."""
+    return np.where(rng(seed).standard_normal((k, 2, ny, nx)) >= 0.0, 1.0, -1.0)
+
+
 def node_coords(nx: int, ny: int, r: float):
     """Physical node centres x = i + 1/2, y = (j + 1/2) r as [ny][nx] arrays."""
     x = np.arange(nx) + 0.5
