@@ -8,17 +8,24 @@
  * of bench.py may load it.  It shares no code, header, table or constant with
  * the CUDA library, and the CUDA library never calls it.
  *
- * The collision follows the sub-steps of Appendix A in the paper's order and
- * notation:
- *   m = P f                      (App. A, pre-collision raw moments, Eq. 62)
- *   m <- S m                     (App. A, scaling, Eq. S-matrix)
- *   m^c = F m                    (App. A, central moments, Eq. 64)
- *   relax with B, Lambda         (App. A, extended equilibria, strain rates)
- *   m~ = F^-1 m~^c               (App. A, post-collision raw moments)
- *   m~ <- S^-1 m~                (App. A, inverse scaling)
- *   f~ = P^-1 m~                 (App. A, Eq. 72)
- *   f(x, t+1) = f~(x - e, t)     (App. A, streaming)
- *   rho, rho u                   (App. A, hydrodynamic fields)
+ * What one time step computes, node by node, in FP64:
+ *   - streaming: each population arrives from the neighbour it points away
+ *     from, or is reflected at a wall (half-way bounce-back, the lid adds
+ *     momentum; reading A3);
+ *   - the density rho and the velocity u (with half the body force, Sec. 4.2);
+ *   - the density gradient from the densities of the same step (reading A1);
+ *   - the collision (Sec. 3-4): the raw and central moments of the nine
+ *     populations by their definitions with the rectangular velocities
+ *     (Eq. 3); the gamma-preconditioned central-moment equilibria (Eq. 14)
+ *     with the grid-anisotropy and cubic-velocity corrections (Eqs. 30-31,
+ *     coefficients of Eqs. 38-40) and the local strain rates (Eqs. 43-48);
+ *     relaxation with the rates of Eq. 11 in the combined (2s, 2d) basis
+ *     (Eqs. 7-8); raw post-collision moments by the binomial theorem; and the
+ *     populations by inverting the moment map, which for the D2Q9 set is a
+ *     product of two 3 x 3 Vandermonde systems.
+ * The moment transforms are written from their definitions rather than from
+ * the matrices P, S, F and their inverses, so that this file and the
+ * matrix-form statement (oracle/matrix_form.py) check each other.
  *
  * Readings taken where the paper is silent, garbled or inconsistent (each is
  * also listed in the design notes):
@@ -86,7 +93,7 @@ typedef struct {
     int bc;
     int drho_off;    /* 1: density-gradient terms set to zero            */
     int corrections; /* 1: extended equilibria (Eq. 30-40); 0: Eq. 14    */
-    int model;       /* 0: PRC-LBM (central moments, Sec. 4.2, App. A);
+    int model;       /* 0: PRC-LBM (central moments, Sec. 4.2);
                         1: PRNR-LBM (raw moments, Sec. 4.1 and Sec. 5.3)   */
     int appendix_literal; /* 1: the strain-rate residuals exactly as App. A
                              prints them (reading A4 not applied); for
@@ -142,37 +149,93 @@ double orc_omega_nu(const orc_params *p)
 }
 
 /* ---------------------------------------------------------------------- */
+/* Moments of a population set.  The nine D2Q9 velocities are the products of
+ * the one-dimensional sets {0, +1, -1} in x and {0, +r, -r} in y (Eq. 3), so a
+ * moment sum_i f_i c_ix^a c_iy^b (a, b = 0, 1, 2) is a tensor product of two
+ * 3 x 3 Vandermonde maps, and the populations follow from the nine moments
+ * by inverting each of them.  Moments here are always taken with the
+ * physical velocities (c_ix, c_iy) = (e_ix, r e_iy/r): the "rectangular" raw
+ * moments k'_ab that the square-lattice moments P f become after the scaling
+ * S (Sec. 4.1). */
+
+/* index of the velocity (vx, vy) with vx in {0, 1, -1} and vy/r in {0, 1, -1} */
+static int dir_of(int vx, int vyb)
+{
+    for (int i = 0; i < 9; i++)
+        if (EX[i] == vx && EYB[i] == vyb) return i;
+    return -1;
+}
+
+/* Populations from their moments m[a][b] = sum_i f_i c_ix^a c_iy^b: solve the
+ * x map for every b, then the y map for every x velocity.  With the values
+ * v in {0, +h, -h}: F(0) = M0 - M2/h^2, F(+h) = (M1/h + M2/h^2)/2,
+ * F(-h) = (M2/h^2 - M1/h)/2 (h = 1 in x, h = r in y). */
+static void populations_from_moments(double r, const double m[3][3], double f[9])
+{
+    double fx[3][3]; /* [x velocity 0, +1, -1][b] */
+    for (int b = 0; b < 3; b++) {
+        fx[0][b] = m[0][b] - m[2][b];
+        fx[1][b] = 0.5 * (m[1][b] + m[2][b]);
+        fx[2][b] = 0.5 * (m[2][b] - m[1][b]);
+    }
+    static const int VAL[3] = {0, 1, -1};
+    const double ir = 1.0 / r, ir2 = 1.0 / (r * r);
+    for (int k = 0; k < 3; k++) {
+        const double *n = fx[k];
+        f[dir_of(VAL[k], 0)] = n[0] - n[2] * ir2;
+        f[dir_of(VAL[k], 1)] = 0.5 * (n[1] * ir + n[2] * ir2);
+        f[dir_of(VAL[k], -1)] = 0.5 * (n[2] * ir2 - n[1] * ir);
+    }
+}
+
+/* Moments about the velocity (ux, uy) by their definition:
+ * m[a][b] = sum_i f_i (c_ix - ux)^a (c_iy - uy)^b; (0, 0) gives the raw moments. */
+static void moments_about(double r, const double f[9], double ux, double uy, double m[3][3])
+{
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) m[a][b] = 0.0;
+    for (int i = 0; i < 9; i++) {
+        const double dx = EX[i] - ux, dy = r * EYB[i] - uy;
+        const double px[3] = {1.0, dx, dx * dx}, py[3] = {1.0, dy, dy * dy};
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) m[a][b] += f[i] * px[a] * py[b];
+    }
+}
+
+/* Raw moments from central moments about (ux, uy), by the binomial theorem:
+ * c_x^a c_y^b = sum_{p <= a, q <= b} C(a,p) C(b,q) ux^(a-p) uy^(b-q)
+ * (c_x - ux)^p (c_y - uy)^q. */
+static void raw_from_central(const double c[3][3], double ux, double uy, double m[3][3])
+{
+    static const double BIN[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 2, 1}};
+    const double pux[3] = {1.0, ux, ux * ux}, puy[3] = {1.0, uy, uy * uy};
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            double v = 0.0;
+            for (int p = 0; p <= a; p++)
+                for (int q = 0; q <= b; q++) v += BIN[a][p] * BIN[b][q] * pux[a - p] * puy[b - q] * c[p][q];
+            m[a][b] = v;
+        }
+}
+
 /* Equilibrium populations f^eq(rho, u): the raw-moment equilibria of Eq. 12
- * (uncorrected), mapped to populations by S^-1 and P^-1 (Eq. S-matrix-inverse,
- * Eq. 72).  Used for the rest weights, field initialisation and the
- * equilibrium-difference bounce-back (reading A3). */
+ * (uncorrected) in the physical velocities, mapped to populations.  Used for
+ * the rest weights, field initialisation and the equilibrium-difference
+ * bounce-back (reading A3). */
 static void equilibrium(const orc_consts *c, double rho, double ux, double uy, double feq[9])
 {
-    const double g = c->p.gamma, cs2 = c->cs2, r = c->p.r;
-    double k00 = rho, k10 = rho * ux, k01 = rho * uy;
-    double k20 = cs2 * rho + rho * ux * ux / g;
-    double k02 = cs2 * rho + rho * uy * uy / g;
-    double k11 = rho * ux * uy / g;
-    double k21 = rho * (cs2 + ux * ux / (g * g)) * uy;
-    double k12 = rho * (cs2 + uy * uy / (g * g)) * ux;
-    double k22 = rho * cs2 * cs2 + rho * cs2 * (ux * ux + uy * uy) + rho * ux * ux * uy * uy;
-    /* S^-1: factor r^-n for k'_mn */
-    k01 /= r;
-    k02 /= r * r;
-    k11 /= r;
-    k21 /= r;
-    k12 /= r * r;
-    k22 /= r * r;
-    /* P^-1 (Eq. 72) */
-    feq[0] = k00 - k20 - k02 + k22;
-    feq[1] = 0.5 * (k10 + k20 - k12 - k22);
-    feq[2] = 0.5 * (k01 + k02 - k21 - k22);
-    feq[3] = 0.5 * (-k10 + k20 + k12 - k22);
-    feq[4] = 0.5 * (-k01 + k02 + k21 - k22);
-    feq[5] = 0.25 * (k11 + k21 + k12 + k22);
-    feq[6] = 0.25 * (-k11 + k21 - k12 + k22);
-    feq[7] = 0.25 * (k11 - k21 - k12 + k22);
-    feq[8] = 0.25 * (-k11 - k21 + k12 + k22);
+    const double g = c->p.gamma, cs2 = c->cs2;
+    double m[3][3];
+    m[0][0] = rho;
+    m[1][0] = rho * ux;
+    m[0][1] = rho * uy;
+    m[2][0] = cs2 * rho + rho * ux * ux / g;
+    m[0][2] = cs2 * rho + rho * uy * uy / g;
+    m[1][1] = rho * ux * uy / g;
+    m[2][1] = rho * (cs2 + ux * ux / (g * g)) * uy;
+    m[1][2] = rho * (cs2 + uy * uy / (g * g)) * ux;
+    m[2][2] = rho * cs2 * cs2 + rho * cs2 * (ux * ux + uy * uy) + rho * ux * ux * uy * uy;
+    populations_from_moments(c->p.r, m, feq);
 }
 
 /* Rest-state populations w_i(r) rho0 with rho0 = 1: f^eq(1, 0). */
@@ -191,8 +254,15 @@ void orc_equilibrium(const orc_params *p, double rho, double ux, double uy, doub
 }
 
 /* ---------------------------------------------------------------------- */
-/* One node's collision, App. A.  diag (if not NULL) receives
- * rho, u_x, u_y, d_x u_x, d_y u_y. */
+/* One node's collision.  The moments come from their definitions (raw
+ * moments of the physical velocities, central moments about the node's
+ * velocity), the preconditioned central-moment equilibria of Eq. 14 carry
+ * the corrections of Eqs. 30-31 with the coefficients of Eqs. 38-40 and the
+ * local strain rates of Eqs. 43-48; the second-order moments relax in the
+ * combined (2s, 2d) basis of Sec. 4.2, and the post-collision central
+ * moments go back to raw moments by the binomial theorem and to populations
+ * by inverting the moment map.  diag (if not NULL) receives rho, u_x, u_y,
+ * d_x u_x, d_y u_y. */
 static void collide(const orc_consts *c, const double f[9], double dxrho, double dyrho,
                     double ft[9], double *diag)
 {
@@ -200,47 +270,30 @@ static void collide(const orc_consts *c, const double f[9], double dxrho, double
     const double r = p->r, g = p->gamma, cs2 = c->cs2;
     const double wxi = p->omega_xi, wnu = c->omega_nu;
 
-    /* -- pre-collision raw moments, square lattice (Eq. 62) -- */
-    double k00 = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    double k10 = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
-    double k01 = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-    double k20 = f[1] + f[3] + f[5] + f[6] + f[7] + f[8];
-    double k02 = f[2] + f[4] + f[5] + f[6] + f[7] + f[8];
-    double k11 = f[5] - f[6] + f[7] - f[8];
-    double k21 = f[5] + f[6] - f[7] - f[8];
-    double k12 = f[5] - f[6] - f[7] + f[8];
-    double k22 = f[5] + f[6] + f[7] + f[8];
+    /* -- raw moments of the physical velocities (what S P f gives) -- */
+    double km[3][3];
+    moments_about(r, f, 0.0, 0.0, km);
+    const double k00 = km[0][0], k10 = km[1][0], k01 = km[0][1];
+    const double k20 = km[2][0], k02 = km[0][2], k11 = km[1][1];
+    const double k21 = km[2][1], k12 = km[1][2], k22 = km[2][2];
 
-    /* -- scale for the rectangular lattice: factor r^n for k'_mn -- */
-    k01 *= r;
-    k02 *= r * r;
-    k11 *= r;
-    k21 *= r;
-    k12 *= r * r;
-    k22 *= r * r;
-
-    /* -- hydrodynamic fields (Eq. hydrodynamicfields) -- */
+    /* -- hydrodynamic fields: density and velocity with half the force (Sec. 4.2) -- */
     const double rho = k00;
     const double ux = (k10 + p->fx / (2.0 * g)) / rho;
     const double uy = (k01 + p->fy / (2.0 * g)) / rho;
 
-    /* -- central moments m^c = F m (binomial transforms, App. A) -- */
-    double c00 = k00;
-    double c10 = k10 - ux * k00;
-    double c01 = k01 - uy * k00;
-    double c20 = k20 - 2 * ux * k10 + ux * ux * k00;
-    double c02 = k02 - 2 * uy * k01 + uy * uy * k00;
-    double c11 = k11 - uy * k10 - ux * k01 + ux * uy * k00;
-    double c21 = k21 - 2 * ux * k11 + ux * ux * k01 - uy * k20 + 2 * ux * uy * k10 - ux * ux * uy * k00;
-    double c12 = k12 - 2 * uy * k11 + uy * uy * k10 - ux * k02 + 2 * ux * uy * k01 - ux * uy * uy * k00;
-    double c22 = k22 - 2 * ux * k12 + ux * ux * k02 - 2 * uy * k21 + 4 * ux * uy * k11
-               - 2 * ux * ux * uy * k01 + uy * uy * k20 - 2 * ux * uy * uy * k10 + ux * ux * uy * uy * k00;
+    /* -- central moments about u, by their definition -- */
+    double cm[3][3];
+    moments_about(r, f, ux, uy, cm);
+    const double c00 = cm[0][0], c10 = cm[1][0], c01 = cm[0][1];
+    const double c20 = cm[2][0], c02 = cm[0][2], c11 = cm[1][1];
+    const double c21 = cm[2][1], c12 = cm[1][2], c22 = cm[2][2];
 
-    /* -- combine second-order moments (operator B) -- */
+    /* -- combined second-order moments (the basis of Eqs. 7-8) -- */
     double c2s = c20 + c02;
     double c2d = c20 - c02;
 
-    /* -- coefficients of the extended equilibria (App. A) -- */
+    /* -- coefficients of the corrected equilibria (Eqs. 38-40, prefactors of Sec. 3.4) -- */
     const double Pg = 4.0 / (g * g) - 1.0 / g;
     const double Qg = 1.0 / (g * g) - 1.0 / g;
     const double Ug = 2.0 / g + 1.0;
@@ -308,7 +361,7 @@ static void collide(const orc_consts *c, const double f[9], double dxrho, double
         double s11 = (1.0 / (g * g) - 1.0 / g) * (fx * uy + fy * ux);
         double s2s = s20 + s02, s2d = s20 - s02;
 
-        /* -- relaxation (App. A), dt = 1 -- */
+        /* -- relaxation with the rates of Eq. 11, dt = 1 -- */
         const double w1 = p->omega_1;
         double t00 = c00;
         double t10 = c10 + w1 * (eq10 - c10) + (1 - w1 / 2) * s10;
@@ -324,17 +377,19 @@ static void collide(const orc_consts *c, const double f[9], double dxrho, double
         double t20 = 0.5 * (t2s + t2d);
         double t02 = 0.5 * (t2s - t2d);
 
-        /* -- post-collision raw moments m~ = F^-1 m~^c (reading A5) -- */
-        m00 = t00;
-        m10 = t10 + ux * t00;
-        m01 = t01 + uy * t00;
-        m20 = t20 + 2 * ux * t10 + ux2 * t00;
-        m02 = t02 + 2 * uy * t01 + uy2 * t00;
-        m11 = t11 + uy * t10 + ux * t01 + ux * uy * t00;
-        m21 = t21 + 2 * ux * t11 + ux2 * t01 + uy * t20 + 2 * ux * uy * t10 + ux2 * uy * t00;
-        m12 = t12 + 2 * uy * t11 + uy2 * t10 + ux * t02 + 2 * ux * uy * t01 + ux * uy2 * t00;
-        m22 = t22 + 2 * ux * t12 + ux2 * t02 + 2 * uy * t21 + 4 * ux * uy * t11
-                   + 2 * ux2 * uy * t01 + uy2 * t20 + 2 * ux * uy2 * t10 + ux2 * uy2 * t00;
+        /* -- post-collision raw moments by the binomial theorem (reading A5) -- */
+        const double tc[3][3] = {{t00, t01, t02}, {t10, t11, t12}, {t20, t21, t22}};
+        double tm[3][3];
+        raw_from_central(tc, ux, uy, tm);
+        m00 = tm[0][0];
+        m10 = tm[1][0];
+        m01 = tm[0][1];
+        m20 = tm[2][0];
+        m02 = tm[0][2];
+        m11 = tm[1][1];
+        m21 = tm[2][1];
+        m12 = tm[1][2];
+        m22 = tm[2][2];
     } else {
         /* PRNR-LBM (Eq. LBErawmomentrectangularlattice): relax the combined
            raw moments B m towards the raw equilibria of Eq. 12, whose second
@@ -366,24 +421,9 @@ static void collide(const orc_consts *c, const double f[9], double dxrho, double
         m02 = 0.5 * (t2s - t2d);
     }
 
-    /* -- inverse scaling: factor r^-n for k~'_mn -- */
-    m01 /= r;
-    m02 /= r * r;
-    m11 /= r;
-    m21 /= r;
-    m12 /= r * r;
-    m22 /= r * r;
-
-    /* -- post-collision populations f~ = P^-1 m~ (Eq. 72) -- */
-    ft[0] = m00 - m20 - m02 + m22;
-    ft[1] = 0.5 * (m10 + m20 - m12 - m22);
-    ft[2] = 0.5 * (m01 + m02 - m21 - m22);
-    ft[3] = 0.5 * (-m10 + m20 + m12 - m22);
-    ft[4] = 0.5 * (-m01 + m02 + m21 - m22);
-    ft[5] = 0.25 * (m11 + m21 + m12 + m22);
-    ft[6] = 0.25 * (-m11 + m21 - m12 + m22);
-    ft[7] = 0.25 * (m11 - m21 - m12 + m22);
-    ft[8] = 0.25 * (-m11 - m21 + m12 + m22);
+    /* -- post-collision populations from their moments -- */
+    const double mt[3][3] = {{m00, m01, m02}, {m10, m11, m12}, {m20, m21, m22}};
+    populations_from_moments(r, mt, ft);
 
     if (diag) {
         diag[0] = rho;
@@ -450,7 +490,7 @@ void orc_destroy(orc_state *s)
 
 /* Fields of a post-collision state: rho = sum f~ (collision conserves mass);
  * rho u = sum f~ e - F/(2 gamma), which equals the velocity the collision used
- * (its first moments gain F/gamma, App. A relaxation of k10, k01). */
+ * (its first moments gain F/gamma in the relaxation, Sec. 4.2). */
 static void fields_from_post(orc_state *s)
 {
     const orc_params *p = &s->c.p;
@@ -508,7 +548,7 @@ void orc_fields(const orc_state *s, double *rho, double *ux, double *uy)
 
 long orc_time(const orc_state *s) { return s->t; }
 
-/* Streaming f(x, t+1) = f~(x - e, t) (App. A), with half-way bounce-back at
+/* Streaming f(x, t+1) = f~(x - e, t) (Sec. 2), with half-way bounce-back at
  * walls (reading A3). */
 static double pull(const orc_state *s, int i, int x, int y)
 {

@@ -82,7 +82,9 @@ def test_device_collision_equals_matrix_form(lib, r, gamma, model):
         dx, dy = (1e-3 * g.standard_normal(2)) if drho else (0.0, 0.0)
         w = S.rest_weights(p)
         gt, w_lib, diag = host_collide(lib, p, model, drho, f - w, dx, dy)
-        assert np.max(np.abs(w_lib - w)) <= 1e-16
+        # the same rest weights up to the rounding order of their sums: two
+        # units in the last place of a weight below 1
+        assert np.max(np.abs(w_lib - w)) <= 2.3e-16
         ft, (rho_o, ux_o, uy_o, _, _) = oracle_collide(f, r, gamma, S.omega_nu(p), dx, dy, p.fx, p.fy,
                                                      omega_3=p.omega_xi)
         # P_gamma and Q_gamma grow like 4 / gamma^2 and the round-off of both
