@@ -197,6 +197,9 @@ lbm_status lbm_sync(lbm_t h);
  * populations of the last step (computed from the stored post-collision
  * populations as sum f~_i e_i - F / (2 gamma)).  rho, ux, uy are [ny][nx]
  * FP64 arrays, device pointers if on_device else host; any may be NULL.
+ * Host arrays in page-locked memory that the device can address
+ * (cudaHostAlloc, cudaHostRegister) are written by the kernel directly over
+ * the host link; other host arrays go through a device staging buffer.
  * Synchronises.
  */
 lbm_status lbm_fields(lbm_t h, double *rho, double *ux, double *uy, int on_device);
@@ -204,7 +207,8 @@ lbm_status lbm_fields(lbm_t h, double *rho, double *ux, double *uy, int on_devic
 /*
  * Set the state to the equilibrium of Eq. 12 (no corrections) of the given
  * fields: f~_i = f^eq_i(rho, u) at every node.  Arrays [ny][nx] FP64, device
- * pointers if on_device else host.  Resets the step counter to 0 and the
+ * pointers if on_device else host (page-locked host arrays are read by the
+ * kernel directly, as in lbm_fields).  Resets the step counter to 0 and the
  * residual snapshot to this u_x.
  */
 lbm_status lbm_init_fields(lbm_t h, const double *rho, const double *ux, const double *uy,
@@ -366,13 +370,35 @@ lbm_status lbm_batch_set_stall(lbm_batch_t b, int slot, long window, double rati
  */
 lbm_status lbm_batch_set_wait_limit(lbm_batch_t b, long long cycles, int hold);
 /*
+ * Tile body of the batch engine (no counterpart in the paper: it chooses how
+ * the same update is executed).  With LBM_BATCH_BODY_AUTO (the default), a
+ * launch of at most 512 active slots, every one with the density-gradient
+ * terms, no body force and the central-moment scheme, in FP32 or FP16
+ * storage, stages the interior of each slot (nodes at least two from every
+ * wall) in 64 x 8 tiles through TMA copies into shared memory, with the same
+ * per-node arithmetic as the single-instance interior kernel on its 64 x 8,
+ * 256-thread variant (lbm_variant_info), and covers the
+ * edge strips with the general tile body; a slot's populations are then
+ * bitwise those of a single handle on that variant.  Otherwise, or with
+ * LBM_BATCH_BODY_GENERAL, every tile takes the general wall-aware body with
+ * L2-served pulls, bitwise that of a single handle on variant -1.
+ * lbm_batch_get_body: *tma = 1 when the next launch takes the TMA-staged body.
+ * EINVAL for any other body value.
+ */
+#define LBM_BATCH_BODY_AUTO 0
+#define LBM_BATCH_BODY_GENERAL 1
+lbm_status lbm_batch_set_body(lbm_batch_t b, int body);
+lbm_status lbm_batch_get_body(lbm_batch_t b, int *tma);
+/*
  * Launch shape of the batch engine (no counterpart in the paper: it chooses
  * how the same update is executed; a slot's results do not depend on it).
  * The persistent grid of lbm_batch_launch is ctas_per_sm x (SM count) CTAs of
- * the 64 x 8 tile body, capped at the number of tiles.
- * lbm_batch_set_ctas_per_sm: 1 <= ctas_per_sm <= *max_ctas_per_sm of
- * lbm_batch_get_ctas_per_sm (the resident CTAs per SM of the kernel), or 0
- * for the default (the maximum); EINVAL otherwise.
+ * the tile body the launch takes, capped at the number of tiles.
+ * lbm_batch_set_ctas_per_sm: 0 <= ctas_per_sm <= the largest resident count
+ * of either body, else EINVAL; 0 selects the maximum of the body a launch
+ * takes, and a larger value than that maximum is taken as the maximum.
+ * lbm_batch_get_ctas_per_sm reports the effective value and the maximum
+ * (*max_ctas_per_sm) for the body of the next launch.
  * lbm_batch_autotune times `steps` steps (1 <= steps <= 100000) of the
  * active slots at every ctas_per_sm from 1 to the maximum, each after one
  * untimed launch of the same length, then restores every slot's populations,

@@ -37,6 +37,8 @@ struct Slot {
     long long max_steps = 0;
     long long stall_window = 0;
     double stall_ratio = 0.0;
+    prc::Interior in;   // TMA body: interior tiling (none: in.ntx == 0) and edge strips
+    prc::Rects edge;
 };
 
 thread_local std::string g_batch_err;
@@ -70,6 +72,11 @@ struct lbm_batch_s {
     long long next_limit;  // lbm_batch_set_wait_limit, for the next launch only
     int next_hold;
     int ctas_per_sm;       // persistent grid: ctas_per_sm x SMs (0: occupancy)
+    // TMA-staged body (k_batch_tma)
+    CUtensorMap *d_tmaps;  // two load descriptors per slot (pop[0], pop[1])
+    CUtensorMap *h_tmaps;  // pinned staging of one slot's pair
+    int occupancy_tma;     // resident CTAs per SM of k_batch_tma (0: not available)
+    int body;              // LBM_BATCH_BODY_*
     std::string err;
 };
 
@@ -107,6 +114,34 @@ lbm_status check_slot(lbm_batch_t b, int slot)
     if (b->in_flight) return bfail(b, LBM_EINVAL, "a launch is in flight: call lbm_batch_wait first");
     return LBM_OK;
 }
+
+// Every active slot allows the specialised body (density-gradient terms, no
+// force, central moments)?
+bool all_spec(lbm_batch_t b)
+{
+    bool any = false;
+    for (int i = 0; i < b->capacity; i++) {
+        const Slot &sl = b->slots[i];
+        if (!sl.used || b->h_dyn[i].state != prc::BATCH_ACTIVE) continue;
+        any = true;
+        if (sl.p.drho != LBM_DRHO_CURRENT || sl.p.fx != 0.0 || sl.p.fy != 0.0 || sl.p.model != LBM_MODEL_PRC)
+            return false;
+    }
+    return any;
+}
+
+// The next launch runs the TMA-staged body: allowed by the body setting, built
+// for this storage type, and every active slot takes the specialised body.
+bool next_is_tma(lbm_batch_t b)
+{
+    if (b->body == LBM_BATCH_BODY_GENERAL || b->occupancy_tma <= 0 || !all_spec(b)) return false;
+    int n = 0;  // the TMA-staged body keeps a table of the launch's instances in shared memory
+    for (int i = 0; i < b->capacity; i++)
+        if (b->slots[i].used && b->h_dyn[i].state == prc::BATCH_ACTIVE) n++;
+    return n <= prc::BT_MAX_INST;
+}
+
+int max_ctas(lbm_batch_t b) { return next_is_tma(b) ? b->occupancy_tma : b->occupancy; }
 
 }  // namespace
 
@@ -158,10 +193,17 @@ lbm_status lbm_batch_create(int capacity, int dtype, void *stream, lbm_batch_t *
         }
         b->own_stream = true;
     }
+    if (ops->batch_tma_prepare) {  // the TMA-staged body: shared-memory opt-in, occupancy
+        if (ops->batch_tma_prepare() != cudaSuccess || ops->batch_tma_occupancy(&b->occupancy_tma) != cudaSuccess) {
+            cudaGetLastError();
+            b->occupancy_tma = 0;
+        }
+    }
     const size_t cbytes = align_up((size_t)capacity * ops->coef_bytes, ALIGN);
     const size_t dbytes = align_up((size_t)capacity * sizeof(BatchDyn), ALIGN);
     const size_t ibytes = align_up((size_t)capacity * sizeof(BatchInst), ALIGN);
-    const size_t tbytes = cbytes + dbytes + ALIGN + ibytes;
+    const size_t mbytes = b->occupancy_tma > 0 ? align_up((size_t)capacity * 2 * sizeof(CUtensorMap), ALIGN) : 0;
+    const size_t tbytes = cbytes + dbytes + ALIGN + ibytes + mbytes;
     if (cudaMalloc(&b->d_tables, tbytes) != cudaSuccess) {
         cudaGetLastError();
         b->err = "device allocation of the batch tables failed";
@@ -171,7 +213,9 @@ lbm_status lbm_batch_create(int capacity, int dtype, void *stream, lbm_batch_t *
     b->d_dyn = reinterpret_cast<BatchDyn *>(b->d_tables + cbytes);
     b->d_ctl = reinterpret_cast<BatchCtl *>(b->d_tables + cbytes + dbytes);
     b->d_inst = reinterpret_cast<BatchInst *>(b->d_tables + cbytes + dbytes + ALIGN);
-    if (cudaMallocHost(&b->h_dyn, capacity * sizeof(BatchDyn)) != cudaSuccess ||
+    b->d_tmaps = mbytes ? reinterpret_cast<CUtensorMap *>(b->d_tables + cbytes + dbytes + ALIGN + ibytes) : nullptr;
+    if ((mbytes && cudaMallocHost(&b->h_tmaps, 2 * sizeof(CUtensorMap)) != cudaSuccess) ||
+        cudaMallocHost(&b->h_dyn, capacity * sizeof(BatchDyn)) != cudaSuccess ||
         cudaMallocHost(&b->h_inst, capacity * sizeof(BatchInst)) != cudaSuccess ||
         cudaMallocHost(&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess ||
         cudaMallocHost(&b->h_coef, ops->coef_bytes) != cudaSuccess) {
@@ -207,6 +251,7 @@ void lbm_batch_destroy(lbm_batch_t b)
     if (b->h_inst) cudaFreeHost(b->h_inst);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     if (b->h_coef) cudaFreeHost(b->h_coef);
+    if (b->h_tmaps) cudaFreeHost(b->h_tmaps);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -247,6 +292,21 @@ lbm_status lbm_batch_add(lbm_batch_t b, const lbm_params *p, double tol, long ma
     // rest state (shifted storage 0) and the snapshot of its u_x
     BCK(b, cudaMemsetAsync(sl.mem, 0, slot_bytes(sl.L), b->stream));
     BCK(b, b->ops->fields(slot_pop(sl, 0), sl.gd, sl.k, nullptr, nullptr, nullptr, slot_snap(sl), b->stream));
+    make_batch_tma_plan(*p, b->ops->tma_padx, sl.in, sl.edge);
+    if (b->d_tmaps && sl.in.ntx > 0) {  // load descriptors of the slot's two sets for the TMA body
+        for (int q = 0; q < 2; q++) {
+            const CUresult r = encode_pop_map(&b->h_tmaps[q], b->ops->elem, slot_pop(sl, q), sl.p.nx, sl.p.ny,
+                                              sl.L.pitch, sl.L.plane, prc::BT_W + 2 * b->ops->tma_padx, prc::BT_H + 2,
+                                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
+            if (r != CUDA_SUCCESS) {
+                cudaFreeAsync(sl.mem, b->stream);
+                sl.mem = nullptr;
+                return bfail(b, LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+            }
+        }
+        BCK(b, cudaMemcpyAsync(b->d_tmaps + 2 * k, b->h_tmaps, 2 * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                               b->stream));
+    }
     b->ops->coef_convert(sl.k, b->h_coef);
     BCK(b, cudaMemcpyAsync(static_cast<char *>(b->d_coefs) + (size_t)k * b->ops->coef_bytes, b->h_coef,
                            b->ops->coef_bytes, cudaMemcpyHostToDevice, b->stream));
@@ -306,8 +366,9 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
     if (s != LBM_OK) return s;
     if (b->in_flight) return bfail(b, LBM_EINVAL, "a launch is in flight: call lbm_batch_wait first");
     if (steps < 1 || steps > (1L << 30)) return bfail(b, LBM_EINVAL, "steps must be in [1, 2^30]");
+    const bool tma = next_is_tma(b);
     // compact list of the active slots, tiles in slot order
-    int n = 0, tiles = 0;
+    int n = 0, tiles = 0, itiles = 0, etiles = 0;
     for (int i = 0; i < b->capacity; i++) {
         const Slot &sl = b->slots[i];
         if (!sl.used || b->h_dyn[i].state != prc::BATCH_ACTIVE) continue;
@@ -330,6 +391,20 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         I.max_steps = sl.max_steps;
         I.stall_window = sl.stall_window;
         I.stall_ratio = sl.stall_ratio;
+        if (tma) {  // interior tiles, then edge tiles; partials in that order
+            I.tmap = b->d_tmaps + 2 * i;
+            I.in = sl.in;
+            I.edge = sl.edge;
+            I.itile_start = itiles;
+            I.etile_start = etiles;
+            // no interior: the whole grid in node-pair tiles of the general kernel
+            if (sl.in.ntx == 0) I.tiles_x = ceil_div(sl.p.nx, prc::PTW);
+            const int ni = sl.in.ntx * sl.in.nty;
+            const int ne = sl.in.ntx == 0 ? I.tiles_x * ceil_div(sl.p.ny, prc::PTH) : sl.edge.start[sl.edge.n];
+            itiles += ni;
+            etiles += ne;
+            I.tiles = ni + ne;
+        }
         tiles += I.tiles;
     }
     if (n == 0) return LBM_OK;  // nothing to do
@@ -360,17 +435,24 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         b->next_limit = 0;
         b->next_hold = 0;
     }
-    int grid = (b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy) * b->num_sms;
+    const int occ = tma ? b->occupancy_tma : b->occupancy;
+    int grid = (b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ) * b->num_sms;
     if (grid > tiles) grid = tiles;
     const int st = (int)steps;
+    auto do_launch = [&](cudaStream_t ls) -> cudaError_t {
+        if (tma)
+            return b->ops->batch_tma_launch(b->d_inst, b->d_coefs, b->d_dyn, n, itiles, etiles, b->d_partials,
+                                            b->d_ctl, st, grid, ls);
+        return b->ops->batch_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials, b->d_ctl, st, grid,
+                                    spec, ls);
+    };
     if (use_graph) {
         cudaStream_t cs;
         BCK(b, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t el = b->ops->batch_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials, b->d_ctl,
-                                                  st, grid, spec, cs);
+            cudaError_t el = do_launch(cs);
             e = cudaStreamEndCapture(cs, &g);
             if (el != cudaSuccess) e = el;
         }
@@ -389,8 +471,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         b->have_gexec = true;
         BCK(b, cudaGraphLaunch(b->gexec, b->stream));
     } else {
-        BCK(b, b->ops->batch_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials, b->d_ctl, st, grid,
-                                    spec, b->stream));
+        BCK(b, do_launch(b->stream));
     }
     b->in_flight = true;
     return LBM_OK;
@@ -400,17 +481,38 @@ lbm_status lbm_batch_set_ctas_per_sm(lbm_batch_t b, int ctas_per_sm)
 {
     lbm_status s = benter(b);
     if (s != LBM_OK) return s;
-    if (ctas_per_sm < 0 || ctas_per_sm > b->occupancy)
-        return bfail(b, LBM_EINVAL, "ctas_per_sm must be in [0, " + std::to_string(b->occupancy) + "]");
+    const int occ = b->occupancy > b->occupancy_tma ? b->occupancy : b->occupancy_tma;
+    if (ctas_per_sm < 0 || ctas_per_sm > occ)
+        return bfail(b, LBM_EINVAL, "ctas_per_sm must be in [0, " + std::to_string(occ) + "]");
     b->ctas_per_sm = ctas_per_sm;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_body(lbm_batch_t b, int body)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    if (body != LBM_BATCH_BODY_AUTO && body != LBM_BATCH_BODY_GENERAL)
+        return bfail(b, LBM_EINVAL, "body must be LBM_BATCH_BODY_AUTO or LBM_BATCH_BODY_GENERAL");
+    b->body = body;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_body(lbm_batch_t b, int *tma)
+{
+    lbm_status s = benter(b);
+    if (s != LBM_OK) return s;
+    if (!tma) return bfail(b, LBM_EINVAL, "null out");
+    *tma = next_is_tma(b) ? 1 : 0;
     return LBM_OK;
 }
 
 lbm_status lbm_batch_get_ctas_per_sm(lbm_batch_t b, int *ctas_per_sm, int *max_ctas_per_sm)
 {
     if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
-    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
-    if (max_ctas_per_sm) *max_ctas_per_sm = b->occupancy;
+    const int occ = max_ctas(b);
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
+    if (max_ctas_per_sm) *max_ctas_per_sm = occ;
     return LBM_OK;
 }
 
@@ -420,7 +522,8 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int steps, int *best, double *ms_pe
     if (s != LBM_OK) return s;
     if (b->in_flight) return bfail(b, LBM_EINVAL, "a launch is in flight: call lbm_batch_wait first");
     if (steps < 1 || steps > 100000) return bfail(b, LBM_EINVAL, "steps must be in [1, 100000]");
-    const int current = b->ctas_per_sm > 0 ? b->ctas_per_sm : b->occupancy;
+    const int occ = max_ctas(b);
+    const int current = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
     // the state a launch changes: the active slots' memory and the dynamic table
     std::vector<int> act;
     size_t bytes = 0;
@@ -463,7 +566,7 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int steps, int *best, double *ms_pe
         rs = LBM_ECUDA;
         msg = "set-up of the timing failed";
     }
-    for (int c = 1; rs == LBM_OK && c <= b->occupancy; c++) {
+    for (int c = 1; rs == LBM_OK && c <= occ; c++) {
         b->ctas_per_sm = c;
         float ms = 0.f;
         // one untimed launch, then a timed one, each from the saved state
@@ -502,7 +605,7 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int steps, int *best, double *ms_pe
         rs = LBM_ECUDA;
         msg = "restore of the state failed";
     }
-    b->ctas_per_sm = rs == LBM_OK ? best_c : (current == b->occupancy ? 0 : current);
+    b->ctas_per_sm = rs == LBM_OK ? best_c : (current == occ ? 0 : current);
     if (rs != LBM_OK) return bfail(b, rs, "lbm_batch_autotune: " + msg);
     if (best) *best = best_c;
     return LBM_OK;

@@ -25,13 +25,16 @@
 #include <type_traits>
 
 #include "prc_pair.cuh"
+#include "prc_tma.cuh"
 
 namespace prc {
 
 // Per-slot coefficient table entry: the collision constants in the collision
 // type and, for the FP32 collision, packed for the pair tile body.
+// 16-byte aligned and sized, so that one bulk copy can bring a slot's entry
+// into shared memory.
 template <typename T>
-struct BatchCoef {
+struct alignas(16) BatchCoef {
     Coef<T> k;
     Coef<F2> k2;
 };
@@ -66,6 +69,15 @@ struct BatchInst {
     long long max_steps;
     long long stall_window;  // steps between stall checkpoints (0: no stall test)
     double stall_ratio;      // stalled when res > stall_ratio * checkpoint residual
+    // TMA-staged tile body (k_batch_tma): the interior tiles (in.ntx x in.nty,
+    // none when in.ntx == 0) staged through the slot's load descriptors, the
+    // edge strips with the general tile body; tiles = interior + edge tiles,
+    // partial sums part_base + (interior tile) and part_base + ntiles_i + (edge tile)
+    const CUtensorMap *tmap;  // descriptors of pop[0] and pop[1] in device memory
+    Interior in;
+    int itile_start;          // first interior tile of this instance in the launch
+    int etile_start;          // first edge tile of this instance in the launch
+    Rects edge;
 };
 
 // Mutable part, updated on the device.
@@ -213,6 +225,68 @@ __device__ __forceinline__ void batch_tile(const BatchInst &I, const BatchCoef<T
     else batch_tile_m<S, T, false>(I, k, parity, lt, epi, partials, bsm);
 }
 
+// Bookkeeping after the tiles of one step: counters, residuals, retirement
+// (one CTA per instance).  Thread 0 reads the instance's state and counter
+// once into shared memory and is the only writer; the barriers keep every
+// branch below uniform across the CTA (a thread that re-read D->t after
+// thread 0 advanced it would take a different branch).  CTAs of 256 threads.
+__device__ __forceinline__ void batch_bookkeeping(const BatchInst *__restrict__ inst, BatchDyn *dyn, int ninst,
+                                                  const double2 *partials, int tid)
+{
+    constexpr int NT = BX * BY;
+    __shared__ long long sh_t;
+    __shared__ int sh_active;
+    for (int j = blockIdx.x; j < ninst; j += gridDim.x) {
+        const BatchInst &I = inst[j];
+        BatchDyn *D = dyn + I.slot;
+        __syncthreads();  // the previous instance's shared values are consumed
+        if (tid == 0) {
+            sh_active = ld_relaxed_i32(&D->state) == BATCH_ACTIVE;
+            sh_t = __ldcg(&D->t) + 1;
+        }
+        __syncthreads();
+        if (!sh_active) continue;
+        const long long t = sh_t;
+        if (t % 20 == 0) {
+            __shared__ double sa[NT], sb[NT];
+            double a = 0.0, b = 0.0;
+            for (int q = tid; q < I.tiles; q += NT) {
+                const double2 v = __ldcg(partials + I.part_base + q);
+                a += v.x;
+                b += v.y;
+            }
+            sa[tid] = a;
+            sb[tid] = b;
+            __syncthreads();
+            for (int w = NT / 2; w > 0; w >>= 1) {
+                if (tid < w) {
+                    sa[tid] += sa[tid + w];
+                    sb[tid] += sb[tid + w];
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                const double res = sqrt(sa[0]), mass = (double)I.gd.nx * (double)I.gd.ny + sb[0];
+                D->res = res;
+                D->mass = mass;
+                D->res_step = t;
+                if (!isfinite(res) || !isfinite(mass)) D->state = BATCH_DIVERGED;
+                else if (res < I.tol) D->state = BATCH_CONVERGED;
+                else if (I.stall_window > 0 && t - D->chk_step >= I.stall_window) {
+                    if (D->chk_step > 0 && res > I.stall_ratio * D->chk_res) D->state = BATCH_STALLED;
+                    D->chk_step = t;
+                    D->chk_res = res;
+                }
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            D->t = t;
+            if (D->state == BATCH_ACTIVE && t >= I.max_steps) D->state = BATCH_MAXSTEPS;
+        }
+    }
+}
+
 // SPEC = 1: every instance of the launch has the density-gradient terms on,
 // no body force and the central-moment scheme, so the tile body is chosen at
 // compile time (a smaller kernel); SPEC = 0 dispatches per instance.
@@ -235,9 +309,10 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
             if (i != ci) {
                 ci = i;
                 // an active instance has completed t0 + s steps; its state may
-                // be changing right now (see the bookkeeping below)
+                // be changing right now (see the bookkeeping below), so the
+                // CTA takes one decision for all its threads
                 t = I.t0 + s;
-                active = ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && t < I.max_steps;
+                active = __syncthreads_and(ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && t < I.max_steps);
             }
             if (!active) continue;
             const bool epi = ((t + 1) % 20) == 0;
@@ -251,62 +326,7 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
             }
         }
         if (!grid_barrier(ctl)) return;
-        // ---- bookkeeping: counters, residuals, retirement (one CTA per instance).
-        // Thread 0 reads the instance's state and counter once into shared
-        // memory and is the only writer; the barriers keep every branch below
-        // uniform across the CTA (a thread that re-read D->t after thread 0
-        // advanced it would take a different branch).
-        __shared__ long long sh_t;
-        __shared__ int sh_active;
-        for (int j = blockIdx.x; j < ninst; j += gridDim.x) {
-            const BatchInst &I = inst[j];
-            BatchDyn *D = dyn + I.slot;
-            __syncthreads();  // the previous instance's shared values are consumed
-            if (tid == 0) {
-                sh_active = ld_relaxed_i32(&D->state) == BATCH_ACTIVE;
-                sh_t = __ldcg(&D->t) + 1;
-            }
-            __syncthreads();
-            if (!sh_active) continue;
-            const long long t = sh_t;
-            if (t % 20 == 0) {
-                __shared__ double sa[BX * BY], sb[BX * BY];
-                double a = 0.0, b = 0.0;
-                for (int q = tid; q < I.tiles; q += BX * BY) {
-                    const double2 v = __ldcg(partials + I.part_base + q);
-                    a += v.x;
-                    b += v.y;
-                }
-                sa[tid] = a;
-                sb[tid] = b;
-                __syncthreads();
-                for (int w = (BX * BY) / 2; w > 0; w >>= 1) {
-                    if (tid < w) {
-                        sa[tid] += sa[tid + w];
-                        sb[tid] += sb[tid + w];
-                    }
-                    __syncthreads();
-                }
-                if (tid == 0) {
-                    const double res = sqrt(sa[0]), mass = (double)I.gd.nx * (double)I.gd.ny + sb[0];
-                    D->res = res;
-                    D->mass = mass;
-                    D->res_step = t;
-                    if (!isfinite(res) || !isfinite(mass)) D->state = BATCH_DIVERGED;
-                    else if (res < I.tol) D->state = BATCH_CONVERGED;
-                    else if (I.stall_window > 0 && t - D->chk_step >= I.stall_window) {
-                        if (D->chk_step > 0 && res > I.stall_ratio * D->chk_res) D->state = BATCH_STALLED;
-                        D->chk_step = t;
-                        D->chk_res = res;
-                    }
-                }
-                __syncthreads();
-            }
-            if (tid == 0) {
-                D->t = t;
-                if (D->state == BATCH_ACTIVE && t >= I.max_steps) D->state = BATCH_MAXSTEPS;
-            }
-        }
+        batch_bookkeeping(inst, dyn, ninst, partials, tid);
         // No grid barrier here: the next step's tiles start while the
         // bookkeeping of this one may still run.  Each instance's bookkeeping
         // is done by one CTA, which alone writes its counter and state; the

@@ -114,6 +114,72 @@ inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
     return pl;
 }
 
+// Interior tiling and edge strips of the batch engine's TMA-staged body
+// (k_batch_tma: BT_W x BT_H tiles at least two nodes from every wall, x origin
+// 16-byte aligned; the rest in strips of the general tile body for CTAs of
+// BT_THREADS).  A grid too small for one interior tile is all strip: in.ntx =
+// in.nty = 0 and one rectangle over the whole grid.  The same rules as
+// make_plan's for the single-instance interior kernel.
+inline void make_batch_tma_plan(const lbm_params &p, int padx, prc::Interior &in, prc::Rects &edge)
+{
+    std::memset(&in, 0, sizeof(in));
+    std::memset(&edge, 0, sizeof(edge));
+    const int W = prc::BT_W, H = prc::BT_H, threads = prc::BT_THREADS;
+    const int ix0 = padx, iy0 = 2;
+    if (p.model == LBM_MODEL_PRC && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
+        const int xlast = ((p.nx - 2 - W) / padx) * padx;
+        const int ylast = p.ny - 2 - H;
+        const int xend = xlast + W, yend = ylast + H;
+        in.ix0 = ix0;
+        in.iy0 = iy0;
+        in.ntx = ceil_div(xend - ix0, W);
+        in.nty = ceil_div(yend - iy0, H);
+        in.xlast = xlast;
+        in.ylast = ylast;
+        add_strip(edge, 0, 0, p.nx, iy0, threads);
+        add_strip(edge, 0, yend, p.nx, p.ny, threads);
+        add_strip(edge, 0, iy0, ix0, yend, threads);
+        add_strip(edge, xend, iy0, p.nx, yend, threads);
+    } else {
+        add_strip(edge, 0, 0, p.nx, p.ny, threads);
+    }
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime's driver entry
+// points (null when unavailable).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn tensor_map_encoder()
+{
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// 3-D tiled descriptor over one population set, (x < nx, y < ny, plane < 9),
+// with a box of bw x bh x 1 elements of `elem` bytes.
+inline CUresult encode_pop_map(CUtensorMap *m, size_t elem, void *base, int nx, int ny, int pitch, size_t plane, int bw,
+                               int bh, CUtensorMapL2promotion l2)
+{
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return CUDA_ERROR_NOT_SUPPORTED;
+    const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                 : (elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * elem, (cuuint64_t)plane * elem};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 struct Layout {
     int pitch;
     size_t plane, pop_bytes, snap_bytes, part_bytes, st_bytes;

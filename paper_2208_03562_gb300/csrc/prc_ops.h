@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "prc_batch.cuh"
+#include "prc_batch_tma.cuh"
 #include "prc_cluster.cuh"
 #include "prc_kernels.cuh"
 #include "prc_tma.cuh"
@@ -36,7 +37,7 @@ struct Plan {
 };
 
 constexpr int MAX_INTERIOR_CTAS = 1024;
-constexpr int MAX_VARIANTS = 4;
+constexpr int MAX_VARIANTS = 5;
 
 // One compiled configuration of the interior kernel.
 struct Variant {
@@ -86,6 +87,13 @@ struct DtypeOps {
     cudaError_t (*cluster_launch)(const void *pop0, const void *pop1, const Grid &gd, const Coef<double> &k,
                                   void *snap, DevStatus *st, long long t0, int n, int nc, int rpc, int smem,
                                   bool drho, bool force, cudaStream_t s);
+    // batch engine with TMA-staged interior tiles (k_batch_tma; FP32 / FP16
+    // storage, null for FP64): shared-memory opt-in (once, outside any stream
+    // capture), resident CTAs per SM, one cooperative launch
+    cudaError_t (*batch_tma_prepare)();
+    cudaError_t (*batch_tma_occupancy)(int *blocks_per_sm);
+    cudaError_t (*batch_tma_launch)(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int itiles,
+                                    int etiles, double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s);
 };
 
 extern const DtypeOps ops_f64, ops_f32, ops_f16;

@@ -298,6 +298,38 @@ cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd
     return cluster_cfg_launch<false, false, false>(a, b, gd, k, k2, sn, st, t0, n, nc, rpc, smem, s);
 }
 
+template <typename TT>
+cudaError_t op_batch_tma_prepare()
+{
+    if constexpr (std::is_same<TT, float>::value)
+        return cudaFuncSetAttribute(k_batch_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_tma_smem<S>());
+    return cudaErrorNotSupported;
+}
+
+template <typename TT>
+cudaError_t op_batch_tma_occupancy(int *blocks_per_sm)
+{
+    if constexpr (std::is_same<TT, float>::value)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_tma<S>, BT_THREADS,
+                                                             batch_tma_smem<S>());
+    *blocks_per_sm = 0;
+    return cudaErrorNotSupported;
+}
+
+template <typename TT>
+cudaError_t op_batch_tma_launch(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int itiles,
+                                int etiles, double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s)
+{
+    if constexpr (std::is_same<TT, float>::value) {
+        const BatchCoef<float> *cf = static_cast<const BatchCoef<float> *>(coefs);
+        void *args[] = {(void *)&inst, (void *)&cf, (void *)&dyn, (void *)&ninst, (void *)&itiles, (void *)&etiles,
+                        (void *)&partials, (void *)&ctl, (void *)&steps};
+        return cudaLaunchCooperativeKernel((const void *)k_batch_tma<S>, dim3(grid), dim3(BT_THREADS), args,
+                                           batch_tma_smem<S>(), s);
+    }
+    return cudaErrorNotSupported;
+}
+
 }  // namespace
 
 #define PRC_VARIANT(W, H, THREADS, MINB) \
@@ -306,6 +338,9 @@ cudaError_t op_cluster_launch(const void *pop0, const void *pop1, const Grid &gd
 const DtypeOps PRC_OPS = {sizeof(S), sizeof(T), 16 / (int)sizeof(S), PRC_NVARIANTS, {PRC_VARIANTS},
                           op_step_general, sizeof(BatchCoef<T>), op_coef_convert, op_batch_occupancy, op_batch_launch,
                           op_init_fields, op_fields, op_set_pop, op_get_pop, op_mass_partial, op_add_rest,
-                          op_cluster_prepare, op_cluster_max_active, op_cluster_launch};
+                          op_cluster_prepare, op_cluster_max_active, op_cluster_launch,
+                          std::is_same<T, float>::value ? op_batch_tma_prepare<T> : nullptr,
+                          std::is_same<T, float>::value ? op_batch_tma_occupancy<T> : nullptr,
+                          std::is_same<T, float>::value ? op_batch_tma_launch<T> : nullptr};
 
 }  // namespace prc

@@ -156,6 +156,54 @@ __device__ __forceinline__ void pull_pair(const S *b, F2 g[9])
     }
 }
 
+// Density (minus rho0) of one ring unit of a staged W x H tile, for the
+// first 2 (W/2) + 2 (H + 2) threads: a pair of the row below or above the
+// tile, or one node of the column left or right of it, into the density tile
+// Rs (node lx of tile row ly at Rs[(ly + 1) RW + lx + 2]).  The same
+// summation order as every other density, so a node's density does not
+// depend on which tile formed it.
+template <typename S, int W, int H, int PE, int BW, int RW, int PADX>
+__device__ __forceinline__ void ring_density(int tid, const S *cur, float *Rs)
+{
+    constexpr int PAIRS = W / 2;
+    if (tid < 2 * PAIRS) {
+        const int ry = tid < PAIRS ? 0 : H + 1;
+        const int rx = 2 * (tid < PAIRS ? tid : tid - PAIRS);
+        F2 gr[9];
+        pull_pair<S, PE>(cur + ry * BW + rx + PADX, gr);
+        *reinterpret_cast<float2 *>(Rs + ry * RW + rx + 2) = sum9(gr).v;
+    } else {
+        const int c = tid - 2 * PAIRS;
+        const int ry = c >> 1, lx = (c & 1) ? W : -1;
+        const S *b = cur + ry * BW + lx + PADX;
+        float gr[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) gr[i] = Pair<S>::one(b + i * PE - ex_of(i));
+        Rs[ry * RW + lx + 2] = sum9(gr);
+    }
+}
+
+// Density gradients (reading A1) of the node pair whose first node's density
+// sits at c = Rs + (ly + 1) RW + x + 2 of a density tile with rows of RW.
+template <int RW>
+__device__ __forceinline__ void pair_gradients(const float *c, float i12, float i12r, F2 &dxr, F2 &dyr)
+{
+    const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
+                 Rr = *reinterpret_cast<const float2 *>(c + 2);
+    const float2 NL = *reinterpret_cast<const float2 *>(c + RW - 2),
+                 NM = *reinterpret_cast<const float2 *>(c + RW),
+                 NR = *reinterpret_cast<const float2 *>(c + RW + 2);
+    const float2 SL = *reinterpret_cast<const float2 *>(c - RW - 2),
+                 SM = *reinterpret_cast<const float2 *>(c - RW),
+                 SR = *reinterpret_cast<const float2 *>(c - RW + 2);
+    // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
+    // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
+    dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
+             (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
+    dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
+             (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
+}
+
 // Persistent step kernel: the interior tiles, NQ pairs of neighbouring nodes
 // per thread (rows ly, ly + H/NQ, ...; H W / 2 = NQ THREADS) with the
 // collision in packed FP32x2 arithmetic, then the edge strips (`edge`,
@@ -301,25 +349,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
 #pragma unroll
             for (int j = 0; j < C::NQ; j++)
                 *reinterpret_cast<float2 *>(Rs + (ly0 + j * DY + 1) * C::RW + x + 2) = sum9(g[j]).v;
-            if (tid < RING) {
-                if (tid < 2 * C::PAIRS) {
-                    const int ry = tid < C::PAIRS ? 0 : H + 1;
-                    const int rx = 2 * (tid < C::PAIRS ? tid : tid - C::PAIRS);
-                    F2 gr[9];
-                    pull_pair<S, PE>(cur + ry * C::BW + rx + C::PADX, gr);
-                    *reinterpret_cast<float2 *>(Rs + ry * C::RW + rx + 2) = sum9(gr).v;
-                } else {
-                    const int c = tid - 2 * C::PAIRS;
-                    const int ry = c >> 1, lx = (c & 1) ? W : -1;
-                    const S *b = cur + ry * C::BW + lx + C::PADX;
-                    float gr[9];
-#pragma unroll
-                    for (int i = 0; i < 9; i++) gr[i] = Pair<S>::one(b + i * PE - ex_of(i));
-                    // same summation order as every other density, so a node's
-                    // density does not depend on which tile formed it
-                    Rs[ry * C::RW + lx + 2] = sum9(gr);
-                }
-            }
+            if (tid < RING) ring_density<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cur, Rs);
         }
         if constexpr (C::TSTORE) {
             // the store of tile it - 2 (issued one tile ago) has read its
@@ -354,24 +384,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
         for (int j = 0; j < C::NQ; j++) {
             const int ly = ly0 + j * DY;
             F2 dxr(0.f), dyr(0.f);
-            if constexpr (DRHO) {
-                const float *c = Rs + (ly + 1) * C::RW + x + 2;
-                const float2 L = *reinterpret_cast<const float2 *>(c - 2), M = *reinterpret_cast<const float2 *>(c),
-                             Rr = *reinterpret_cast<const float2 *>(c + 2);
-                const float2 NL = *reinterpret_cast<const float2 *>(c + C::RW - 2),
-                             NM = *reinterpret_cast<const float2 *>(c + C::RW),
-                             NR = *reinterpret_cast<const float2 *>(c + C::RW + 2);
-                const float2 SL = *reinterpret_cast<const float2 *>(c - C::RW - 2),
-                             SM = *reinterpret_cast<const float2 *>(c - C::RW),
-                             SR = *reinterpret_cast<const float2 *>(c - C::RW + 2);
-                const float i12 = kf.inv12, i12r = kf.inv12r;
-                // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
-                // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
-                dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
-                         (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
-                dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
-                         (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
-            }
+            if constexpr (DRHO) pair_gradients<C::RW>(Rs + (ly + 1) * C::RW + x + 2, kf.inv12, kf.inv12r, dxr, dyr);
             F2 ux, uy, drho;
             collide<F2, DRHO, FORCE>(k, g[j], dxr, dyr, ux, uy, drho);
             const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);

@@ -97,6 +97,8 @@ def load():
         "lbm_batch_set_stall": [B, C.c_int, C.c_long, C.c_double],
         "lbm_batch_set_wait_limit": [B, C.c_longlong, C.c_int],
         "lbm_batch_set_ctas_per_sm": [B, C.c_int],
+        "lbm_batch_set_body": [B, C.c_int],
+        "lbm_batch_get_body": [B, C.POINTER(C.c_int)],
         "lbm_batch_get_ctas_per_sm": [B, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "lbm_batch_autotune": [B, C.c_int, C.POINTER(C.c_int), _D],
         "lbm_batch_launch": [B, C.c_long, C.c_int],
@@ -133,11 +135,14 @@ def exported_symbols():
                  "lbm_create_p", "lbm_create_ex", "lbm_set_stream", "lbm_destroy", "lbm_last_error",
                  "lbm_step", "lbm_run", "lbm_residual", "lbm_mass", "lbm_info", "lbm_sync", "lbm_fields",
                  "lbm_init_fields", "lbm_set_populations", "lbm_get_populations", "lbm_save_bytes",
-                 "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info", "lbm_get_variant",
+                 "lbm_save", "lbm_load", "lbm_variant_count", "lbm_variant_info",
+                 "lbm_get_variant",
                  "lbm_set_variant", "lbm_autotune", "lbm_step_noalloc", "lbm_batch_create",
                  "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_instance_bytes", "lbm_batch_add",
                  "lbm_batch_remove", "lbm_batch_set_stall", "lbm_batch_set_wait_limit",
-                 "lbm_batch_set_ctas_per_sm", "lbm_batch_get_ctas_per_sm", "lbm_batch_autotune", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run", "lbm_batch_query",
+                 "lbm_batch_set_ctas_per_sm", "lbm_batch_get_ctas_per_sm", "lbm_batch_set_body",
+                 "lbm_batch_get_body", "lbm_batch_autotune", "lbm_batch_launch", "lbm_batch_wait", "lbm_batch_run",
+                 "lbm_batch_query",
                  "lbm_batch_fields", "lbm_batch_set_populations", "lbm_batch_get_populations",
                  "lbm_batch_mass", "lbm_batch_set_mass", "lbm_set_mass"):
         if hasattr(L, name):
@@ -432,6 +437,7 @@ class Lbm:
 # batched engine
 
 SLOT_ACTIVE, SLOT_CONVERGED, SLOT_DIVERGED, SLOT_MAXSTEPS, SLOT_EMPTY, SLOT_STALLED = range(6)
+BATCH_BODY_AUTO, BATCH_BODY_GENERAL = 0, 1
 SLOT_NAMES = ["ACTIVE", "CONVERGED", "DIVERGED", "MAXSTEPS", "EMPTY", "STALLED"]
 
 
@@ -500,6 +506,18 @@ class Batch:
     @ctas_per_sm.setter
     def ctas_per_sm(self, value: int):
         _bcheck(load().lbm_batch_set_ctas_per_sm(self.b, int(value)), self.b)
+
+    def set_body(self, body: int):
+        """BATCH_BODY_AUTO (TMA-staged interior tiles when the launch allows
+        them) or BATCH_BODY_GENERAL (lbm_batch_set_body)."""
+        _bcheck(load().lbm_batch_set_body(self.b, int(body)), self.b)
+
+    @property
+    def tma_body(self) -> bool:
+        """The next launch takes the TMA-staged body (lbm_batch_get_body)."""
+        t = C.c_int()
+        _bcheck(load().lbm_batch_get_body(self.b, C.byref(t)), self.b)
+        return bool(t.value)
 
     @property
     def max_ctas_per_sm(self) -> int:

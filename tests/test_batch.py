@@ -80,6 +80,7 @@ def test_each_slot_retires_on_its_own_residual():
            I.Cavity(30, 60, 2.0, 0.25, 20.0, 0.02, "f32")]
     tols = [1e-6, 1e-5, 1e-7]
     b = L.Batch(4, L.F32)
+    b.set_body(L.BATCH_BODY_GENERAL)
     slots = [b.add(L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32), t, 500000)
              for c, t in zip(cav, tols)]
     active = len(slots)
@@ -125,6 +126,7 @@ def test_diverging_slot_does_not_disturb_the_others():
     good = I.Cavity(64, 32, 0.5, 0.5, 100.0, 0.03, "f32")
     mk = lambda c: L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32)
     b = L.Batch(4, L.F32)
+    b.set_body(L.BATCH_BODY_GENERAL)
     sb = b.add(mk(bad), 1e-7, 4000)
     sg = b.add(mk(good), 1e-30, 1000)
     b.run(4000)
@@ -140,6 +142,7 @@ def test_diverging_slot_does_not_disturb_the_others():
 def test_add_and_remove_between_launches():
     mk = lambda nx, ny: L.lbm_params_init(nx, ny, 1.0, 0.5, 0.02, 0.03, L.F32)
     b = L.Batch(3, L.F32)
+    b.set_body(L.BATCH_BODY_GENERAL)
     s0 = b.add(mk(40, 30), 1e-30, 10 ** 6)
     s1 = b.add(mk(50, 20), 1e-30, 10 ** 6)
     b.run(30)
@@ -159,16 +162,20 @@ def test_add_and_remove_between_launches():
     b.remove(s3)
 
 
-def test_grid_barrier_wait_runs_out_and_reports_timeout():
+@pytest.mark.parametrize("body", [L.BATCH_BODY_AUTO, L.BATCH_BODY_GENERAL])
+def test_grid_barrier_wait_runs_out_and_reports_timeout(body):
     """Failure detection without a fault: the first CTA withholds its arrival
     at the first grid barrier (a flag that nothing clears), every other CTA's
     bounded wait runs out (limit about 1 ms), the launch ends with
     LBM_ETIMEOUT, no slot's state has moved, and the device and the batch
-    stay usable: the next launch steps as if the failed one had not been."""
+    stay usable: the next launch steps as if the failed one had not been.
+    Both tile bodies (TMA-staged and general) share the barrier."""
     mk = lambda nx, ny: L.lbm_params_init(nx, ny, 0.5, 0.3, 0.01, 0.03, L.F32)
     b = L.Batch(2, L.F32)
+    b.set_body(body)
     s0 = b.add(mk(64, 32), 1e-30, 10 ** 6)
     s1 = b.add(mk(200, 90), 1e-30, 10 ** 6)
+    assert b.tma_body == (body == L.BATCH_BODY_AUTO)
     f0 = [b.populations(s) for s in (s0, s1)]
     b.set_wait_limit(2_000_000, hold=True)
     with pytest.raises(L.LbmError) as e:
@@ -181,7 +188,7 @@ def test_grid_barrier_wait_runs_out_and_reports_timeout():
     assert b.run(40) == 2  # the default limit again, one launch only
     for s, (nx, ny) in zip((s0, s1), ((64, 32), (200, 90))):
         h = L.Lbm(mk(nx, ny))
-        h.variant = L.VARIANT_GENERAL
+        h.variant = 0 if body == L.BATCH_BODY_AUTO else L.VARIANT_GENERAL
         h.step(40)
         info, st = b.query(s)
         assert info.step == 40 and np.array_equal(b.populations(s), h.populations())
@@ -260,6 +267,7 @@ def test_specialised_kernel_equals_single_instances(dtype):
         (517, 211, 0.25, 0.2, 0.005, 0.02),
     ]
     b = L.Batch(len(cases), dtype)
+    b.set_body(L.BATCH_BODY_GENERAL)
     slots, refs = [], []
     for k, (nx, ny, r, gamma, nu, u) in enumerate(cases):
         p = L.lbm_params_init(nx, ny, r, gamma, nu, u, dtype)
@@ -272,6 +280,7 @@ def test_specialised_kernel_equals_single_instances(dtype):
         h.set_populations(f0)
         slots.append(s)
         refs.append(h)
+    assert not b.tma_body
     for n in (1, 18, 41):  # crossing residual steps
         b.run(n)
         for s, h in zip(slots, refs):
@@ -283,6 +292,116 @@ def test_specialised_kernel_equals_single_instances(dtype):
                 assert info.residual == h.residual() and info.mass == h.info().mass
     for h in refs:
         h.close()
+
+
+# nx, ny, r, gamma, nu, u_lid: several interior tiles both ways with a shifted
+# last tile column and row (300 x 100, 200 x 90, 517 x 211), a single interior
+# tile row or column (134 x 26, 72 x 12 and 70 x 19 in FP32; the last two have
+# none in FP16, whose tile origins align to 8 nodes), no interior tile (33 x 40)
+TMA_CASES = [
+    (300, 100, 0.5, 0.3, 0.01, 0.03),
+    (200, 90, 2.0, 0.1, 0.01, 0.02),
+    (134, 26, 1.0, 0.6, 0.02, 0.05),
+    (70, 19, 1.0, 1.0, 0.02, 0.05),
+    (517, 211, 0.25, 0.2, 0.005, 0.02),
+    (72, 12, 0.5, 0.5, 0.01, 0.02),
+    (33, 40, 1.6, 0.4, 0.01, 0.02),
+]
+
+
+def batch_tile_variant(dtype):
+    """The interior-kernel variant with the batch body's tile: 64 x 8 nodes,
+    256 threads."""
+    for v in range(L.lbm_variant_count(dtype)):
+        if L.lbm_variant_info(dtype, v)[:3] == (64, 8, 256):
+            return v
+    raise AssertionError("no 64 x 8 interior-kernel variant")
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F16])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_tma_body_equals_single_instances_on_the_interior_kernel(dtype, use_graph):
+    """The TMA-staged batch body runs, per node, what a single handle runs on
+    the interior kernel with the same 64 x 8 tile: the staged pulls, the density ring, the
+    gradients and the packed collision in its interior tiles, the general
+    tile body on its edge strips, the node-pair tiles of the general kernel
+    on grids without interior tiles.  Every slot's populations must equal
+    that handle's bitwise, with the step counts; the residual and mass sum
+    the same node terms grouped by tile instead of by CTA, so they agree to
+    FP64 round-off."""
+    b = L.Batch(len(TMA_CASES), dtype)
+    slots, refs = [], []
+    for k, (nx, ny, r, gamma, nu, u) in enumerate(TMA_CASES):
+        p = L.lbm_params_init(nx, ny, r, gamma, nu, u, dtype)
+        w = S.rest_weights(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u))
+        f0 = w[:, None, None] + I.noise(1700 + k, (9, ny, nx), 1e-3)
+        s = b.add(p, 0.0, 10 ** 6)
+        b.set_populations(s, f0)
+        h = L.Lbm(p)
+        h.variant = batch_tile_variant(dtype)
+        h.set_populations(f0)
+        slots.append(s)
+        refs.append(h)
+    assert b.tma_body
+    for n in (1, 18, 41, 60):  # crossing residual steps
+        b.launch(n, use_graph)
+        assert b.wait() == len(TMA_CASES)
+        for s, h in zip(slots, refs):
+            h.step(n)
+            info, st = b.query(s)
+            assert st == L.SLOT_ACTIVE and info.step == h.info().step
+            assert np.array_equal(b.populations(s), h.populations()), (b.shapes[s], info.step)
+            if info.residual_step:
+                hi = h.info()
+                assert abs(info.residual - hi.residual) <= 1e-9 * hi.residual
+                assert abs(info.mass - hi.mass) <= 1e-12 * hi.mass
+    for h in refs:
+        h.close()
+
+
+def test_tma_body_retires_where_single_handles_stop():
+    """Retirement on the residual with the TMA-staged body: each slot stops at
+    the step where a single handle on the interior kernel stops, with the
+    same populations."""
+    cav = [I.Cavity(150, 60, 0.5, 0.5, 50.0, 0.03, "f32"), I.Cavity(100, 100, 1.0, 1.0, 100.0, 0.05, "f32"),
+           I.Cavity(90, 130, 2.0, 0.25, 60.0, 0.02, "f32")]
+    tols = [1e-5, 1e-5, 2e-6]
+    b = L.Batch(4, L.F32)
+    slots = [b.add(L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32), t, 500000)
+             for c, t in zip(cav, tols)]
+    assert b.tma_body
+    while b.run(5000):
+        pass
+    for c, t, s in zip(cav, tols, slots):
+        info, st = b.query(s)
+        assert st == L.SLOT_CONVERGED and info.residual < t
+        h = L.Lbm(L.lbm_params_init(c.nx, c.ny, c.r, c.gamma, c.nu, c.u_lid, L.F32))
+        h.variant = 0
+        status, steps = h.run(t, 500000)
+        assert status == L.OK and steps == info.step
+        assert np.array_equal(b.populations(s), h.populations())
+        h.close()
+
+
+def test_tma_body_and_general_body_agree():
+    """The two tile bodies of the batch engine take the same steps up to FP32
+    round-off (different tile shapes, the same node arithmetic)."""
+    out = []
+    for body in (L.BATCH_BODY_AUTO, L.BATCH_BODY_GENERAL):
+        b = L.Batch(len(TMA_CASES), L.F32)
+        b.set_body(body)
+        slots = []
+        for k, (nx, ny, r, gamma, nu, u) in enumerate(TMA_CASES):
+            p = L.lbm_params_init(nx, ny, r, gamma, nu, u, L.F32)
+            w = S.rest_weights(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u))
+            s = b.add(p, 0.0, 10 ** 6)
+            b.set_populations(s, w[:, None, None] + I.noise(2700 + k, (9, ny, nx), 1e-3))
+            slots.append(s)
+        assert b.tma_body == (body == L.BATCH_BODY_AUTO)
+        b.run(45)
+        out.append([b.populations(s) for s in slots])
+    for a, g in zip(*out):
+        assert np.max(np.abs(a - g)) < 1e-7
 
 
 def test_autotune_restores_state_when_a_wait_runs_out():
