@@ -274,41 +274,21 @@ struct DevTmp {
     }
 };
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 // 3-D tiled descriptors over one population set: (x < nx, y < ny, plane < 9).
 // Load: box = interior tile + ring, x widened to 16-byte aligned edges.
 // Store: box = interior tile (its x origin is 16-byte aligned, and it lies
 // inside the grid, so no store starts at a negative coordinate).
 lbm_status make_tmaps(lbm_t h)
 {
-    static EncodeTiledFn encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-            return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled not available");
-        encode = reinterpret_cast<EncodeTiledFn>(fn);
-    }
+    if (!tensor_map_encoder()) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled not available");
     const size_t elem = h->ops->elem;
-    const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                 : (elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-    const cuuint64_t dims[3] = {(cuuint64_t)h->p.nx, (cuuint64_t)h->p.ny, 9};
-    const cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * elem, (cuuint64_t)h->L.plane * elem};
     const prc::Variant &v = h->ops->variants[h->variant];
-    const cuuint32_t box[3] = {(cuuint32_t)(v.w + 2 * h->ops->tma_padx), (cuuint32_t)(v.h + 2), 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
     for (int b = 0; b < 2; b++) {
-        CUresult r = encode(&h->tmap[b], dt, 3, h->pop[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = encode_pop_map(&h->tmap[b], elem, h->pop[b], h->p.nx, h->p.ny, h->L.pitch, h->L.plane,
+                                    v.w + 2 * h->ops->tma_padx, v.h + 2, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
         if (r != CUDA_SUCCESS) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-        const cuuint32_t sbox[3] = {(cuuint32_t)v.w, (cuuint32_t)v.h, 1};
-        r = encode(&h->tmap_st[b], dt, 3, h->pop[b], dims, strides, sbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        r = encode_pop_map(&h->tmap_st[b], elem, h->pop[b], h->p.nx, h->p.ny, h->L.pitch, h->L.plane, v.w, v.h,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE);
         if (r != CUDA_SUCCESS) return fail(h, LBM_ECUDA, "cuTensorMapEncodeTiled (store) failed (" + std::to_string((int)r) + ")");
     }
     return LBM_OK;
@@ -733,11 +713,28 @@ lbm_status lbm_set_mass(lbm_t h, double mass)
     return LBM_OK;
 }
 
+// Page-locked host memory the device can address (cudaHostAlloc /
+// cudaHostRegister; with unified addressing its host pointer is also its
+// device pointer): kernels then read or write it directly over the host link,
+// with no staging buffer and no separate copy.
+bool device_addressable_host(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 lbm_status lbm_fields(lbm_t h, double *rho, double *ux, double *uy, int on_device)
 {
     lbm_status s = enter(h);
     if (s != LBM_OK) return s;
     const size_t n = (size_t)h->p.nx * h->p.ny;
+    if (!on_device && device_addressable_host(rho) && device_addressable_host(ux) && device_addressable_host(uy))
+        on_device = 1;  // page-locked host buffers: written by the kernel itself
     if (on_device) {
         CK(h, h->ops->fields(cur_pop(h), h->gd, h->k, rho, ux, uy, nullptr, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
@@ -764,6 +761,8 @@ lbm_status lbm_init_fields(lbm_t h, const double *rho, const double *ux, const d
     DevTmp tmp;
     tmp.s = h->stream;
     const double *d[3] = {rho, ux, uy};
+    if (!on_device && device_addressable_host(rho) && device_addressable_host(ux) && device_addressable_host(uy))
+        on_device = 1;  // page-locked host buffers: read by the kernel itself
     if (!on_device) {
         CK(h, cudaMallocAsync(&tmp.p, 3 * n * sizeof(double), h->stream));
         double *b = static_cast<double *>(tmp.p);
