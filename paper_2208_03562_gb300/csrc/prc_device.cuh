@@ -168,8 +168,24 @@ PRC_HD T sum9(const T g[9])
 // second-order moments and the sources agree between the frames), and those
 // of orders 3-4 are the raw equilibria of Eq. 12 (rates 1) instead of the
 // binomial transform of the central ones.
-template <typename T, bool DRHO, bool FORCE, bool RAW = false>
-PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out, T &drho_out)
+//
+// The collision falls into two halves: collide_moments forms everything that
+// does not depend on the density gradient (moments, velocity, the
+// non-equilibrium moments and the strain-rate system's matrix), and
+// collide_relax the rest.  A kernel may run the first half while it waits for
+// the densities of its neighbours; collide() is the two in sequence, the same
+// operations in the same order.
+template <typename T>
+struct Moments {
+    T s00, jx, jy, ux, uy;            // density deviation, momentum, velocity
+    T ux2, uy2, uxy, rux2, ruy2, ruxy;  // their products
+    T sp, sm, c2s00;                  // rho (u_x^2 +- u_y^2), c^2 s00
+    T n2s, n2d, n11;                  // non-equilibrium second-order central moments
+    T m11, m22, m12, nm21, idet;      // strain-rate system (see collide_moments)
+};
+
+template <typename T, bool FORCE>
+PRC_HD void collide_moments(const Coef<T> &k, const T g[9], Moments<T> &M)
 {
     // square-lattice raw moments of the deviations (Eq. 62 applied to g)
     const T a13 = vsub(g[1], g[3]), a56 = vsub(g[5], g[6]), a87 = vsub(g[8], g[7]);
@@ -208,14 +224,6 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
         n11 = vfma(uy, k.hx, vfma(ux, k.hy, n11));
     }
 
-    // local strain rates (Eqs. 43-48, R per Eq. 45); nebr = -e_b,rho, nesr = -e_s,rho
-    T nebr = splat<T>(0.0), nesr = splat<T>(0.0);
-    if (DRHO) {
-        const T Adx = vmul(vmul(k.Ax, ux), dxr), Bdy = vmul(vmul(k.By, uy), dyr);
-        nebr = vadd(Adx, Bdy);
-        nesr = vsub(Adx, Bdy);
-    }
-    const T R2s = vsub(n2s, nebr), R2d = vsub(n2d, nesr);
     // The two unknowns X, Y of the strain-rate system (Eqs. 43-44) solve
     //   (Cb0 rho + a_x) X + (Cb0 rho + a_y) Y = R2s,
     //   (Cs0 rho + d_x) X + (n_y - Cs0 rho) Y = R2d,
@@ -235,6 +243,26 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
     const T m11 = vfma(k.pp, qp, k.e1), m22 = vfma(k.pm, qp, k.e3);
     const T m12 = vfma(k.pm, qm, k.e2), nm21 = vfma(k.npp, qm, k.ne2);
     const T idet = vrcp(vfma(m11, m22, vmul(m12, nm21)));
+    M = Moments<T>{s00, jx, jy, ux, uy, ux2, uy2, uxy, rux2, ruy2, ruxy, sp, sm, c2s00, n2s, n2d, n11,
+                   m11, m22, m12, nm21, idet};
+}
+
+template <typename T, bool DRHO, bool FORCE, bool RAW = false>
+PRC_HD void collide_relax(const Coef<T> &k, const Moments<T> &M, T g[9], T dxr, T dyr, T &ux_out, T &uy_out,
+                          T &drho_out)
+{
+    const T s00 = M.s00, jx = M.jx, jy = M.jy, ux = M.ux, uy = M.uy;
+    const T ux2 = M.ux2, uy2 = M.uy2, uxy = M.uxy, rux2 = M.rux2, ruy2 = M.ruy2, ruxy = M.ruxy;
+    const T sp = M.sp, sm = M.sm, c2s00 = M.c2s00, n2s = M.n2s, n2d = M.n2d, n11 = M.n11;
+    const T m11 = M.m11, m22 = M.m22, m12 = M.m12, nm21 = M.nm21, idet = M.idet;
+    // local strain rates (Eqs. 43-48, R per Eq. 45); nebr = -e_b,rho, nesr = -e_s,rho
+    T nebr = splat<T>(0.0), nesr = splat<T>(0.0);
+    if (DRHO) {
+        const T Adx = vmul(vmul(k.Ax, ux), dxr), Bdy = vmul(vmul(k.By, uy), dyr);
+        nebr = vadd(Adx, Bdy);
+        nesr = vsub(Adx, Bdy);
+    }
+    const T R2s = vsub(n2s, nebr), R2d = vsub(n2d, nesr);
     const T Xs = vmul(vsub(vmul(m22, R2s), vmul(m12, R2d)), idet);
     const T Xd = vmul(vfma(m11, R2d, vmul(nm21, R2s)), idet);
 
@@ -312,6 +340,14 @@ PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out
     ux_out = ux;
     uy_out = uy;
     drho_out = s00;
+}
+
+template <typename T, bool DRHO, bool FORCE, bool RAW = false>
+PRC_HD void collide(const Coef<T> &k, T g[9], T dxr, T dyr, T &ux_out, T &uy_out, T &drho_out)
+{
+    Moments<T> M;
+    collide_moments<T, FORCE>(k, g, M);
+    collide_relax<T, DRHO, FORCE, RAW>(k, M, g, dxr, dyr, ux_out, uy_out, drho_out);
 }
 
 }  // namespace prc

@@ -356,6 +356,14 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
             // output buffer, which this tile's collision refills
             if (tid == 0) bulk_wait_read_all();
         }
+        // FP16 storage: the half of the collision that needs no density
+        // gradient runs before the barrier, while the warps with ring
+        // densities to form are still at it
+        Moments<F2> mom[C::NQ];
+        if constexpr (C::TSTORE) {
+#pragma unroll
+            for (int j = 0; j < C::NQ; j++) collide_moments<F2, FORCE>(k, g[j], mom[j]);
+        }
         // every pull from `cur` is done and R[s] is complete
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -386,7 +394,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
             F2 dxr(0.f), dyr(0.f);
             if constexpr (DRHO) pair_gradients<C::RW>(Rs + (ly + 1) * C::RW + x + 2, kf.inv12, kf.inv12r, dxr, dyr);
             F2 ux, uy, drho;
-            collide<F2, DRHO, FORCE>(k, g[j], dxr, dyr, ux, uy, drho);
+            if constexpr (!C::TSTORE) collide_moments<F2, FORCE>(k, g[j], mom[j]);
+            collide_relax<F2, DRHO, FORCE>(k, mom[j], g[j], dxr, dyr, ux, uy, drho);
             const long long o = (long long)(y0 + ly) * gd.pitch + (x0 + x);
             if constexpr (C::TSTORE) {
                 S *ob = (s ? out1 : out0) + ly * W + x;
