@@ -55,6 +55,7 @@ struct BatchTileInst {
     long long t;  // the instance's step count in this step
     int itile_start, ntx, xlast, ylast;
     int slot, active;
+    int etile_start;
 };
 
 constexpr int BT_MAX_INST = 512;  // instances of a launch of k_batch_tma at most
@@ -186,6 +187,7 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
             e.ylast = I.in.ylast;
             e.slot = I.slot;
             e.active = ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && e.t < I.max_steps;
+            e.etile_start = I.etile_start;
             tinst[k] = e;
         }
         __syncthreads();
@@ -270,10 +272,11 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
         }
         // ---- edge strips: general tile body, L2-coherent loads, density tile
         // in R; the CTA's edge tiles strided over the global edge-tile list
+        // (their instances found in the shared table, not in global memory)
         {
             int ei = 0;
             for (int e = blockIdx.x; e < total_etiles; e += gridDim.x) {
-                while (ei + 1 < ninst && e >= inst[ei + 1].etile_start) ei++;
+                while (ei + 1 < ninst && e >= tinst[ei + 1].etile_start) ei++;
                 if (!tinst[ei].active) continue;
                 const BatchInst &I = inst[ei];
                 const long long t = tinst[ei].t;
