@@ -106,3 +106,67 @@ def test_central_moments_stay_stable_where_raw_moments_diverge():
     prnr = SW.solve(nx, ny, r, gamma, nu, u, 1e-9, 200_000, "f32", model=1)
     assert prc["status"] != "diverged", prc
     assert prnr["status"] == "diverged", prnr
+
+
+def _study_oracle():
+    with open(os.path.join(GOLDEN, "study_oracle.json")) as fh:
+        return json.load(fh)["runs"]
+
+
+def _proj_rel(rec, fields):
+    """Relative L2 distance of (u_x, u_y) from the oracle's, estimated from the
+    stored random projections (their mean square difference estimates the
+    squared distance)."""
+    from paper_2208_03562_gb300 import inputs as I
+    _, ux, uy = fields
+    w = I.projection_signs(rec["proj_seed"], len(rec["proj"]), rec["nx"], rec["ny"])
+    p = np.array([np.sum(w[k, 0] * ux) + np.sum(w[k, 1] * uy) for k in range(len(rec["proj"]))])
+    return math.sqrt(np.mean((p - np.array(rec["proj"])) ** 2)) / math.hypot(rec["norm_ux"], rec["norm_uy"])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", ["shallow_gamma1", "shallow_gamma0.1"])
+def test_convergence_study_on_the_fp64_path_reproduces_the_oracle(name):
+    """The convergence study's solve (sweep.solve) on the FP64 path against
+    the FP64 oracle's run of the same shallow cavity (Sec. 5.2: 100 x 125,
+    r = 0.2, Re 100, Ma 0.06) to the residual 1e-8: the same step count to
+    the step, and the same steady field to the FP64 parity bar (1e-10)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    rec = _study_oracle()[name]
+    r = SW.solve(rec["nx"], rec["ny"], rec["r"], rec["gamma"], rec["nu"], rec["u_lid"], rec["tol"], 5_000_000,
+                 "f64", want_fields=True)
+    assert r["status"] == "converged" and rec["status"] == "converged"
+    assert r["steps"] == rec["steps"], (r["steps"], rec["steps"])
+    assert abs(r["residual"] - rec["residual"]) <= 1e-6 * rec["residual"]
+    assert _proj_rel(rec, r["fields"]) <= 1e-10
+
+
+@pytest.mark.gpu
+def test_grid_saving_study_on_the_fp64_path_reproduces_the_oracle():
+    """The grid-saving study (sweep.grid_saving_study) on the FP64 path: both
+    grids take the oracle's step counts to the residual 1e-7, and the
+    centre-line differences the study reports equal those of the oracle's
+    profiles to 1e-10 of the lid speed."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    recs = _study_oracle()
+    res = SW.grid_saving_study(tol=1e-7, dtype="f64")
+    prof = {}
+    for name in ("rect_r0.2_100x125", "square_r1_400x100"):
+        run, rec = res["runs"][name], recs[name]
+        assert run["status"] == "converged" and run["steps"] == rec["steps"], (name, run["steps"], rec["steps"])
+        prof[name] = rec
+    a, b = prof["rect_r0.2_100x125"], prof["square_r1_400x100"]
+    ys_a = (np.arange(a["ny"]) + 0.5) / a["ny"]
+    ys_b = (np.arange(b["ny"]) + 0.5) / b["ny"]
+    xs_a = (np.arange(a["nx"]) + 0.5) / a["nx"]
+    xs_b = (np.arange(b["nx"]) + 0.5) / b["nx"]
+    du = np.max(np.abs(np.array(a["u_centre"]) / a["u_lid"] -
+                       np.interp(ys_a, ys_b, np.array(b["u_centre"]) / b["u_lid"])))
+    dv = np.max(np.abs(np.array(a["v_centre"]) / a["u_lid"] -
+                       np.interp(xs_a, xs_b, np.array(b["v_centre"]) / b["u_lid"])))
+    assert abs(res["max_abs_diff_u_centreline_over_U"] - du) <= 1e-10
+    assert abs(res["max_abs_diff_v_centreline_over_U"] - dv) <= 1e-10
