@@ -64,6 +64,12 @@
  *       its second-order equilibria; they are the same expressions as in
  *       the central scheme, with the strain rates of
  *       Eq. 45, which is written for the central non-equilibrium moments.
+ *   A13 storage_f32 = 1 keeps the arithmetic in FP64 and rounds only what is
+ *       stored between steps, as a reduced-precision run stores it: the
+ *       deviation of each post-collision population from the rest state
+ *       w_i(r), to the nearest float32.  The paper fixes no precision; this
+ *       is the oracle of the FP32 storage format, used where the FP64 run
+ *       and an FP32-storage run of an unstable flow part ways.
  *
  * State layout: the post-collision populations f~ of the last completed
  * step, f~[i][y][x], i = 0..8, y = 0..ny-1, x = 0..nx-1 (x fastest).  One
@@ -98,6 +104,11 @@ typedef struct {
     int appendix_literal; /* 1: the strain-rate residuals exactly as App. A
                              prints them (reading A4 not applied); for
                              reporting the size of that reading only    */
+    int storage_f32; /* 1: the stored post-collision populations are
+                        rounded, every step, to the nearest float32
+                        deviation from the rest state w_i(r) (the
+                        shifted FP32 storage of a reduced-precision
+                        run); the arithmetic stays FP64            */
 } orc_params;
 
 /* Per-run constants derived once from the parameters. */
@@ -106,6 +117,7 @@ typedef struct {
     double q;        /* Eq. 2: q = min(1, r)                      */
     double cs2;      /* q^2 c_s*^2 with c_s*^2 = 1/3 (Eq. 1-2)     */
     double omega_nu; /* from nu = gamma q^2 c_s*^2 (1/w - 1/2)     */
+    double w[9];     /* rest state w_i(r) (storage_f32 only)       */
 } orc_consts;
 
 typedef struct {
@@ -459,6 +471,7 @@ orc_state *orc_create(const orc_params *p)
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     if (!s) return NULL;
     make_consts(p, &s->c);
+    equilibrium(&s->c, 1.0, 0.0, 0.0, s->c.w);
     size_t n = (size_t)p->nx * (size_t)p->ny;
     s->ft = (double *)calloc(9 * n, sizeof(double));
     s->f = (double *)calloc(9 * n, sizeof(double));
@@ -636,6 +649,8 @@ void orc_step(orc_state *s, long nsteps)
                 for (int i = 0; i < 9; i++) f[i] = s->f[(size_t)i * n + k];
                 if (!p->drho_off) orc_density_gradient(s, x, y, &dxr, &dyr);
                 collide(&s->c, f, dxr, dyr, ft, NULL);
+                if (p->storage_f32)
+                    for (int i = 0; i < 9; i++) ft[i] = s->c.w[i] + (double)(float)(ft[i] - s->c.w[i]);
                 for (int i = 0; i < 9; i++) s->ft[(size_t)i * n + k] = ft[i];
             }
         s->t++;

@@ -23,7 +23,7 @@ class _Params(C.Structure):
         ("omega_12", C.c_double), ("omega_22", C.c_double),
         ("fx", C.c_double), ("fy", C.c_double),
         ("bc", C.c_int), ("drho_off", C.c_int), ("corrections", C.c_int), ("model", C.c_int),
-        ("appendix_literal", C.c_int),
+        ("appendix_literal", C.c_int), ("storage_f32", C.c_int),
     ]
 
 
@@ -48,6 +48,7 @@ class OracleParams:
     corrections: int = 1
     model: int = 0  # 0: PRC-LBM (central moments); 1: PRNR-LBM (raw moments)
     appendix_literal: int = 0  # 1: App. A's strain-rate residuals as printed (reading A4 not applied)
+    storage_f32: int = 0  # 1: stored populations rounded to float32 deviations from w_i(r) every step
 
     def c(self) -> _Params:
         d = asdict(self)
