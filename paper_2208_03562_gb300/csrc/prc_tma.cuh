@@ -211,9 +211,9 @@ __device__ __forceinline__ void pair_gradients(const float *c, float i12, float 
 // launch is one time step.
 //
 // FP16 storage: the collided pairs go to a shared output tile (two buffers,
-// alternating by tile), and thread 0 writes a tile with nine tiled TMA stores
+// alternating by tile), and the producer writes a tile with nine tiled TMA stores
 // right after the next tile's barrier (every thread has written and fenced
-// its part by then); before a buffer is refilled, thread 0 waits until the
+// its part by then); before a buffer is refilled, the producer waits until the
 // stores issued from it have read it.  This replaces nine global stores and
 // their 64-bit address arithmetic per pair with shared-memory stores at fixed
 // offsets.  FP32 storage stores from registers (its shared memory is taken by
@@ -224,12 +224,14 @@ __device__ __forceinline__ void pair_gradients(const float *c, float i12, float 
 // of one ring unit for the first 2 W/2 + 2 (H + 2) threads) goes to the
 // density tile R[it & 1]; after one barrier the thread forms the density
 // gradients from R[it & 1] and collides its pairs.  That barrier is the only
-// one per tile: after it the stage just read is free, so thread 0 refills it
+// one per tile: after it the stage just read is free, so the producer refills it
 // with the copies of the tile after next (two tiles in flight during the
 // collision), and the density tile alternates between two buffers, so a
 // thread may start the next tile while others still read this tile's
 // densities (the next write of R[it & 1] comes after the next barrier, which
-// every thread reaches only once its collision of this tile is done).
+// every thread reaches only once its collision of this tile is done).  The
+// producer is lane 0 of the last warp, which forms no ring densities, so that
+// its copies and stores do not add to the ring warps' share of a tile.
 template <typename S, int W, int H, int THREADS, int MINB, bool DRHO, bool EPI, bool FORCE>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUtensorMap tdst,
@@ -239,7 +241,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
 {
     using C = TmaCfg<S, W, H, THREADS>;
     static_assert(C::NQ >= 1 && C::NQ * THREADS == H * C::PAIRS, "whole node pairs per thread");
-    static_assert(2 * C::PAIRS + 2 * C::RH <= THREADS, "one ring unit per thread at most");
+    static_assert(2 * C::PAIRS + 2 * C::RH <= THREADS - 32, "one ring unit per thread at most, none in the producer's warp");
     static_assert(C::R_BYTES >= srho_floats(THREADS) * (int)sizeof(float), "density tile too small for the strips");
     static_assert(C::OUT_PLANE % 128 == 0, "TMA store sources start on 128-byte boundaries");
     if (st->stop) return;
@@ -259,6 +261,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
     constexpr int RING = 2 * C::PAIRS + 2 * C::RH;        // ring units: 2 rows of pairs, 2 columns
 
     const int tid = threadIdx.x;
+    constexpr int PROD = THREADS - 32;
     // this thread's pairs in the tile: column x, rows ly0 + j H / NQ
     const int ly0 = tid / C::PAIRS, x = 2 * (tid - ly0 * C::PAIRS);
     constexpr int DY = H / C::NQ;
@@ -290,7 +293,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
     auto order = [&](int q) { return in.rev ? ntiles - 1 - q : q; };
     RedAcc<float> acc;
     int tile = blockIdx.x;
-    if (tid == 0) {
+    if (tid == PROD) {
         if (tile < ntiles) issue(order(tile), stage0, &bar[0]);
         if (tile + (int)gridDim.x < ntiles) issue(order(tile + gridDim.x), stage1, &bar[1]);
     }
@@ -354,7 +357,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
         if constexpr (C::TSTORE) {
             // the store of tile it - 2 (issued one tile ago) has read its
             // output buffer, which this tile's collision refills
-            if (tid == 0) bulk_wait_read_all();
+            if (tid == PROD) bulk_wait_read_all();
         }
         // FP16 storage: the half of the collision that needs no density
         // gradient runs before the barrier, while the warps with ring
@@ -366,7 +369,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
         }
         // every pull from `cur` is done and R[s] is complete
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
+            if (tid == PROD) {
                 atomicExch(&st->timeout, 1);
                 atomicExch(&st->stop, 1);
                 // the copies of the next tile into the other stage may be outstanding
@@ -375,7 +378,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
             }
             return;
         }
-        if (tid == 0) {
+        if (tid == PROD) {
             if (tile + 2 * (int)gridDim.x < ntiles) issue(order(tile + 2 * gridDim.x), cur, &bar[s]);
             if constexpr (C::TSTORE) {
                 // store the previous tile: every thread wrote and fenced its
@@ -420,7 +423,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
     }
     __syncthreads();  // every collision is done: R is free
     if constexpr (C::TSTORE) {
-        if (tid == 0 && it > 0) {  // the last tile's store
+        if (tid == PROD && it > 0) {  // the last tile's store
             const S *o = ((it - 1) & 1) ? out1 : out0;
 #pragma unroll
             for (int i = 0; i < 9; i++) tma_store_3d(&tdst, o + i * OPE, px0, py0, i);
@@ -440,7 +443,7 @@ k_step_tma(const __grid_constant__ CUtensorMap tsrc, const __grid_constant__ CUt
         if (tid == 0) partials[blockIdx.x] = make_double2(a, b);
     }
     if constexpr (C::TSTORE) {
-        if (tid == 0) bulk_wait_all();  // the output tiles stay allocated until the stores are done
+        if (tid == PROD) bulk_wait_all();  // the output tiles stay allocated until the stores are done
     }
 }
 
