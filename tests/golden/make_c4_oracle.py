@@ -7,7 +7,14 @@ Calls only the oracle (oracle/stepper.py) and the seeded input generators.
 For every cavity, from rest, 1000 steps in blocks of 20 with the Sec. 5.2
 residual after each block (a non-finite residual ends the run: diverged);
 for the eight smallest cavities, also the run to the residual 1e-7 (the
-sweep's tolerance) or divergence.  Each record keeps the status, the steps,
+sweep's tolerance) or divergence.  Each cavity also runs from a rest state
+perturbed by relative noise of 1e-7 per population (the rounding level of
+FP32 storage; inputs.noise(8000 + i, ...)); the relative L2 distance of its
+velocity from the unperturbed run at step 1000 is the oracle's own
+sensitivity to perturbations of that size ("sensitivity"; infinite when
+either run diverged).  A cavity whose flow is unstable or chaotic amplifies
+such perturbations, so its step-1000 state is not fixed to the FP32 parity
+bar by the parameters alone.  Each record keeps the status, the steps,
 the residual, ||u_x||_2, ||u_y||_2 and the total mass, (u_x, u_y) at 16
 sampled nodes (inputs.sample_nodes(9000 + i, ...)) and 8 random projections
 of (u_x, u_y) (inputs.projection_signs(7000 + i, ...)), from which a test
@@ -16,7 +23,7 @@ it.
 
   python tests/golden/make_c4_oracle.py [--workers N]
 
-Takes about a quarter of an hour on 8 host cores (one oracle thread per
+Takes about three quarters of an hour on 8 host cores (one oracle thread per
 cavity, cavities in parallel).
 """
 import argparse
@@ -61,21 +68,40 @@ def _record(o, i, cav, status, steps, res):
     return rec
 
 
+PERTURB = 1e-7
+
+
 def job(args):
     i, kind = args
     from oracle import stepper as S
     from paper_2208_03562_gb300 import inputs as I
     S.num_threads(1)
     cav = I.batched_sweep(seed=0, n=256)[i]
-    o = S.Oracle(S.OracleParams(nx=cav.nx, ny=cav.ny, r=cav.r, gamma=cav.gamma, nu=cav.nu, u_lid=cav.u_lid))
+    par = S.OracleParams(nx=cav.nx, ny=cav.ny, r=cav.r, gamma=cav.gamma, nu=cav.nu, u_lid=cav.u_lid)
+    o = S.Oracle(par)
     t = time.perf_counter()
     if kind == "step1000":
         steps, res = o.run(0.0, STEPS)
         status = "diverged" if not math.isfinite(res) else "finite"
+        # the same run from a perturbed rest state
+        p = S.Oracle(par)
+        w = S.rest_weights(par)
+        p.set_populations(w[:, None, None] * (1.0 + I.noise(8000 + i, (9, cav.ny, cav.nx), PERTURB)))
+        _, res_p = p.run(0.0, STEPS)
+        if status == "finite" and math.isfinite(res_p):
+            _, ux, uy = o.fields()
+            _, px, py = p.fields()
+            num = math.fsum(((px - ux) ** 2 + (py - uy) ** 2).ravel())
+            den = math.fsum((ux * ux + uy * uy).ravel())
+            sens = math.sqrt(num / den)
+        else:
+            sens = math.inf
     else:
         steps, res = o.run(TOL, MAX_STEPS)
         status = "diverged" if not math.isfinite(res) else ("converged" if res < TOL else "maxsteps")
     rec = _record(o, i, cav, status, steps, res)
+    if kind == "step1000":
+        rec["sensitivity"] = _g(sens) if math.isfinite(sens) else "inf"
     rec["oracle_s"] = round(time.perf_counter() - t, 1)
     return i, kind, rec
 
@@ -92,6 +118,7 @@ def main():
     out = {"source": __doc__.strip().splitlines()[0],
            "workload": "inputs.batched_sweep(seed=0, n=256), FP64 oracle from rest",
            "n_samples": N_SAMPLES, "n_proj": N_PROJ, "steps": STEPS, "tol": TOL, "max_steps": MAX_STEPS,
+           "perturbation": PERTURB,
            "step1000": {}, "converge": {}}
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(a.workers) as pool:
