@@ -372,14 +372,15 @@ lbm_status lbm_batch_set_wait_limit(lbm_batch_t b, long long cycles, int hold);
 /*
  * Tile body of the batch engine (no counterpart in the paper: it chooses how
  * the same update is executed).  With LBM_BATCH_BODY_AUTO (the default), a
- * launch of at most 512 active slots, every one with the density-gradient
- * terms, no body force and the central-moment scheme, in FP32 or FP16
- * storage, stages the interior of each slot (nodes at least two from every
- * wall) in 64 x 8 tiles through TMA copies into shared memory, with the same
- * per-node arithmetic as the single-instance interior kernel on its 64 x 8,
- * 256-thread variant (lbm_variant_info), and covers the
- * edge strips with the general tile body; a slot's populations are then
- * bitwise those of a single handle on that variant.  Otherwise, or with
+ * launch of at most 512 active slots, every one a cavity (LBM_BC_CAVITY) with
+ * the density-gradient terms, no body force and the central-moment scheme,
+ * in FP32 or FP16 storage, stages every 64 x 8 tile of each slot through TMA
+ * copies into shared memory: tiles clear of the walls with the arithmetic of
+ * the single-instance interior kernel, tiles at a wall with wall-aware
+ * streaming from the staged windows.  Every node computes what a single
+ * handle on the 64 x 8, 256-thread interior-kernel variant
+ * (lbm_variant_info) computes for it, so a slot's populations are bitwise
+ * that handle's.  Otherwise, or with
  * LBM_BATCH_BODY_GENERAL, every tile takes the general wall-aware body with
  * L2-served pulls, bitwise that of a single handle on variant -1.
  * lbm_batch_get_body: *tma = 1 when the next launch takes the TMA-staged body.

@@ -37,8 +37,6 @@ struct Slot {
     long long max_steps = 0;
     long long stall_window = 0;
     double stall_ratio = 0.0;
-    prc::Interior in;   // TMA body: interior tiling (none: in.ntx == 0) and edge strips
-    prc::Rects edge;
 };
 
 thread_local std::string g_batch_err;
@@ -73,8 +71,8 @@ struct lbm_batch_s {
     int next_hold;
     int ctas_per_sm;       // persistent grid: ctas_per_sm x SMs (0: occupancy)
     // TMA-staged body (k_batch_tma)
-    CUtensorMap *d_tmaps;  // two load descriptors per slot (pop[0], pop[1])
-    CUtensorMap *h_tmaps;  // pinned staging of one slot's pair
+    CUtensorMap *d_tmaps;  // four load descriptors per slot: interior box of pop[0], pop[1]; wall box of both
+    CUtensorMap *h_tmaps;  // pinned staging of one slot's four
     int occupancy_tma;     // resident CTAs per SM of k_batch_tma (0: not available)
     int body;              // LBM_BATCH_BODY_*
     std::string err;
@@ -124,7 +122,8 @@ bool all_spec(lbm_batch_t b)
         const Slot &sl = b->slots[i];
         if (!sl.used || b->h_dyn[i].state != prc::BATCH_ACTIVE) continue;
         any = true;
-        if (sl.p.drho != LBM_DRHO_CURRENT || sl.p.fx != 0.0 || sl.p.fy != 0.0 || sl.p.model != LBM_MODEL_PRC)
+        if (sl.p.drho != LBM_DRHO_CURRENT || sl.p.fx != 0.0 || sl.p.fy != 0.0 || sl.p.model != LBM_MODEL_PRC ||
+            sl.p.bc != LBM_BC_CAVITY)
             return false;
     }
     return any;
@@ -202,7 +201,7 @@ lbm_status lbm_batch_create(int capacity, int dtype, void *stream, lbm_batch_t *
     const size_t cbytes = align_up((size_t)capacity * ops->coef_bytes, ALIGN);
     const size_t dbytes = align_up((size_t)capacity * sizeof(BatchDyn), ALIGN);
     const size_t ibytes = align_up((size_t)capacity * sizeof(BatchInst), ALIGN);
-    const size_t mbytes = b->occupancy_tma > 0 ? align_up((size_t)capacity * 2 * sizeof(CUtensorMap), ALIGN) : 0;
+    const size_t mbytes = b->occupancy_tma > 0 ? align_up((size_t)capacity * 4 * sizeof(CUtensorMap), ALIGN) : 0;
     const size_t tbytes = cbytes + dbytes + ALIGN + ibytes + mbytes;
     if (cudaMalloc(&b->d_tables, tbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -214,7 +213,7 @@ lbm_status lbm_batch_create(int capacity, int dtype, void *stream, lbm_batch_t *
     b->d_ctl = reinterpret_cast<BatchCtl *>(b->d_tables + cbytes + dbytes);
     b->d_inst = reinterpret_cast<BatchInst *>(b->d_tables + cbytes + dbytes + ALIGN);
     b->d_tmaps = mbytes ? reinterpret_cast<CUtensorMap *>(b->d_tables + cbytes + dbytes + ALIGN + ibytes) : nullptr;
-    if ((mbytes && cudaMallocHost(&b->h_tmaps, 2 * sizeof(CUtensorMap)) != cudaSuccess) ||
+    if ((mbytes && cudaMallocHost(&b->h_tmaps, 4 * sizeof(CUtensorMap)) != cudaSuccess) ||
         cudaMallocHost(&b->h_dyn, capacity * sizeof(BatchDyn)) != cudaSuccess ||
         cudaMallocHost(&b->h_inst, capacity * sizeof(BatchInst)) != cudaSuccess ||
         cudaMallocHost(&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess ||
@@ -292,19 +291,18 @@ lbm_status lbm_batch_add(lbm_batch_t b, const lbm_params *p, double tol, long ma
     // rest state (shifted storage 0) and the snapshot of its u_x
     BCK(b, cudaMemsetAsync(sl.mem, 0, slot_bytes(sl.L), b->stream));
     BCK(b, b->ops->fields(slot_pop(sl, 0), sl.gd, sl.k, nullptr, nullptr, nullptr, slot_snap(sl), b->stream));
-    make_batch_tma_plan(*p, b->ops->tma_padx, sl.in, sl.edge);
-    if (b->d_tmaps && sl.in.ntx > 0) {  // load descriptors of the slot's two sets for the TMA body
-        for (int q = 0; q < 2; q++) {
-            const CUresult r = encode_pop_map(&b->h_tmaps[q], b->ops->elem, slot_pop(sl, q), sl.p.nx, sl.p.ny,
-                                              sl.L.pitch, sl.L.plane, prc::BT_W + 2 * b->ops->tma_padx, prc::BT_H + 2,
-                                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
+    if (b->d_tmaps) {  // load descriptors of the slot's two sets for the TMA body: interior and wall boxes
+        for (int q = 0; q < 4; q++) {
+            const CUresult r = encode_pop_map(&b->h_tmaps[q], b->ops->elem, slot_pop(sl, q & 1), sl.p.nx, sl.p.ny,
+                                              sl.L.pitch, sl.L.plane, prc::BT_W + 2 * b->ops->tma_padx,
+                                              q < 2 ? prc::BT_H + 2 : prc::BT_H + 4, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
             if (r != CUDA_SUCCESS) {
                 cudaFreeAsync(sl.mem, b->stream);
                 sl.mem = nullptr;
                 return bfail(b, LBM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
             }
         }
-        BCK(b, cudaMemcpyAsync(b->d_tmaps + 2 * k, b->h_tmaps, 2 * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+        BCK(b, cudaMemcpyAsync(b->d_tmaps + 4 * k, b->h_tmaps, 4 * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                                b->stream));
     }
     b->ops->coef_convert(sl.k, b->h_coef);
@@ -368,7 +366,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
     if (steps < 1 || steps > (1L << 30)) return bfail(b, LBM_EINVAL, "steps must be in [1, 2^30]");
     const bool tma = next_is_tma(b);
     // compact list of the active slots, tiles in slot order
-    int n = 0, tiles = 0, itiles = 0, etiles = 0;
+    int n = 0, tiles = 0;
     for (int i = 0; i < b->capacity; i++) {
         const Slot &sl = b->slots[i];
         if (!sl.used || b->h_dyn[i].state != prc::BATCH_ACTIVE) continue;
@@ -391,20 +389,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
         I.max_steps = sl.max_steps;
         I.stall_window = sl.stall_window;
         I.stall_ratio = sl.stall_ratio;
-        if (tma) {  // interior tiles, then edge tiles; partials in that order
-            I.tmap = b->d_tmaps + 2 * i;
-            I.in = sl.in;
-            I.edge = sl.edge;
-            I.itile_start = itiles;
-            I.etile_start = etiles;
-            // no interior: the whole grid in node-pair tiles of the general kernel
-            if (sl.in.ntx == 0) I.tiles_x = ceil_div(sl.p.nx, prc::PTW);
-            const int ni = sl.in.ntx * sl.in.nty;
-            const int ne = sl.in.ntx == 0 ? I.tiles_x * ceil_div(sl.p.ny, prc::PTH) : sl.edge.start[sl.edge.n];
-            itiles += ni;
-            etiles += ne;
-            I.tiles = ni + ne;
-        }
+        if (tma) I.tmap = b->d_tmaps + 4 * i;  // the same 64 x 8 tiles, staged through the slot's descriptors
         tiles += I.tiles;
     }
     if (n == 0) return LBM_OK;  // nothing to do
@@ -441,7 +426,7 @@ lbm_status lbm_batch_launch(lbm_batch_t b, long steps, int use_graph)
     const int st = (int)steps;
     auto do_launch = [&](cudaStream_t ls) -> cudaError_t {
         if (tma)
-            return b->ops->batch_tma_launch(b->d_inst, b->d_coefs, b->d_dyn, n, itiles, etiles, b->d_partials,
+            return b->ops->batch_tma_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials,
                                             b->d_ctl, st, grid, ls);
         return b->ops->batch_launch(b->d_inst, b->d_coefs, b->d_dyn, n, tiles, b->d_partials, b->d_ctl, st, grid,
                                     spec, ls);

@@ -69,15 +69,10 @@ struct BatchInst {
     long long max_steps;
     long long stall_window;  // steps between stall checkpoints (0: no stall test)
     double stall_ratio;      // stalled when res > stall_ratio * checkpoint residual
-    // TMA-staged tile body (k_batch_tma): the interior tiles (in.ntx x in.nty,
-    // none when in.ntx == 0) staged through the slot's load descriptors, the
-    // edge strips with the general tile body; tiles = interior + edge tiles,
-    // partial sums part_base + (interior tile) and part_base + ntiles_i + (edge tile)
-    const CUtensorMap *tmap;  // descriptors of pop[0] and pop[1] in device memory
-    Interior in;
-    int itile_start;          // first interior tile of this instance in the launch
-    int etile_start;          // first edge tile of this instance in the launch
-    Rects edge;
+    // TMA-staged tile body (k_batch_tma): the same tiles, staged through the
+    // slot's load descriptors in device memory, interior box (tile + ring) of
+    // pop[0] and pop[1], then wall box (two rows taller) of both
+    const CUtensorMap *tmap;
 };
 
 // Mutable part, updated on the device.

@@ -1,26 +1,38 @@
-// prc_batch_tma.cuh -- the batch engine with TMA-staged interior tiles.
+// prc_batch_tma.cuh -- the batch engine with TMA-staged tiles.
 //
 // Same contract as k_batch (prc_batch.cuh): one cooperative persistent launch
 // advances every active instance by up to `steps` time steps, a bounded grid
 // barrier per step, per-instance bookkeeping and retirement.  The tiles differ:
-//   * the interior of each instance (nodes at least two from every wall) is
-//     covered by 64 x 8 tiles whose source windows -- the tile plus a one-node
-//     ring, shifted by -e_i, one per population plane -- come into shared
-//     memory by nine tiled TMA copies through the instance's own descriptors,
-//     two tiles in flight per CTA, exactly as in the single-instance interior
-//     kernel k_step_tma (one node pair per thread, the same pulls, density
-//     ring, gradients and packed FP32x2 collision, so an instance's
-//     populations are bitwise those of a single handle on that kernel);
-//   * the edge strips use the general tile body with L2-coherent loads, and
-//     a grid too small for one interior tile is covered by the general
-//     kernel's 64 x 8 node-pair tiles (as a single handle on variant 0 does).
+// each instance is covered by 64 x 8 node tiles at origins (64 tx, 8 ty), the
+// last column and row reaching past the grid, and every tile's source windows
+// -- one per population plane, shifted by -e_i -- come into shared memory by
+// nine tiled TMA copies through the instance's own descriptors, two tiles in
+// flight per CTA, one node pair per thread.
+//   * A tile whose nodes and one-node density ring all lie at least one node
+//     inside the walls (an interior tile) runs the single-instance interior
+//     kernel's tile body (k_step_tma): windows of the tile plus the ring, the
+//     same pulls, density ring, gradients and packed FP32x2 collision.
+//   * Any other tile (a wall tile) takes windows two rows taller (one more
+//     row below and above), which hold, for every node of the tile and of its
+//     ring, both its pulls and all nine of its own populations.  Streaming is
+//     then wall-aware from shared memory: a source outside the grid is
+//     replaced by the node's own opposite population, with the moving-lid
+//     term on the two diagonal links from above the top wall (half-way
+//     bounce-back, reading A3).  Ring nodes inside the grid form their
+//     density the same way; the density gradient reads its eight neighbours
+//     at positions clamped into the grid (the nearest fluid node's density
+//     beyond a wall, reading A1); only nodes inside the grid are stored.
+// Every node computes what the general tile body computes for it (the same
+// pulls, density sums, stencil and collision, in the same order), so an
+// instance's populations are bitwise those of a single handle on the 64 x 8
+// interior-kernel variant, whose edge strips take the general tile body.
 // The CTAs take the global tile list strided by the grid size; in each, one
 // producer thread walks its tiles two ahead, skips the tiles of retired
 // instances, stages each tile's windows and its instance's coefficients, and
-// hands the tile to the CTA through a record in shared memory that the
-// tile's barrier publishes.  Used when every instance of the launch
-// has the density-gradient terms, no body force and the central-moment
-// scheme, FP32 or FP16 storage.
+// hands the tile to the CTA through a record in shared memory that the tile's
+// barrier publishes.  Used when every instance of the launch is a cavity with
+// the density-gradient terms, no body force and the central-moment scheme,
+// FP32 or FP16 storage.
 #pragma once
 
 #include "prc_batch.cuh"
@@ -28,22 +40,35 @@
 namespace prc {
 
 constexpr int BT_W = 64, BT_H = 8, BT_THREADS = 256;
+static_assert(BT_W == PTW && BT_H == BY, "the batch tiles of both bodies share one tiling and one partial-sum layout");
 
 template <typename S>
-using BatchTmaCfg = TmaCfg<S, BT_W, BT_H, BT_THREADS>;
+struct BatchTmaCfg {
+    static constexpr int W = BT_W, H = BT_H;
+    static constexpr int PADX = 16 / (int)sizeof(S);  // 16-byte aligned box start
+    static constexpr int BW = W + 2 * PADX;           // box width (elements)
+    static constexpr int BH = H + 2;                  // interior tiles: tile + ring rows
+    static constexpr int BHW = H + 4;                 // wall tiles: one more row below and above
+    static constexpr int BOX_BYTES = BW * BH * (int)sizeof(S);
+    static constexpr int BOXW_BYTES = BW * BHW * (int)sizeof(S);
+    static constexpr int PLANE_BYTES = (BOXW_BYTES + 127) / 128 * 128;  // one plane slot holds either box
+    static constexpr int STAGE_BYTES = 9 * PLANE_BYTES;
+    static constexpr int RW = W + 4, RH = H + 2;  // density tile: node lx of row ly at (ly + 1) RW + lx + 2
+    static constexpr int R_BYTES = (RW * RH * 4 + 127) / 128 * 128;
+    static constexpr int PAIRS = W / 2;
+};
 
 // Order this thread's later async-proxy (TMA) reads of global memory after
 // the generic-proxy writes it has synchronised with (the previous step's
 // stores by every CTA, made visible by the grid barrier).
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// A staged interior tile: global tile index (-1: none), instance, step count
-// of the instance, tile origin (x0, y0) and nominal origin (ox, oy; the last
-// row / column of tiles is shifted back, see Interior).
+// A staged tile: global tile index (-1: none), instance, step count of the
+// instance, origin, and whether it is a wall tile.
 struct BatchTile {
     int q, i;
     long long t;
-    int x0, y0, ox, oy;
+    int x0, y0, wall;
 };
 
 // What the tile walk needs of an instance, copied into shared memory at the
@@ -51,11 +76,10 @@ struct BatchTile {
 // is active in that step), so that the producer never waits on global
 // memory for it.
 struct BatchTileInst {
-    const CUtensorMap *tmap;
-    long long t;  // the instance's step count in this step
-    int itile_start, ntx, xlast, ylast;
-    int slot, active;
-    int etile_start;
+    const CUtensorMap *tmap;  // [interior box: set 0, set 1; wall box: set 0, set 1]
+    long long t;              // the instance's step count in this step
+    int tile_start, ntx, nx, ny;
+    int slot, active, lid_on, pad;
 };
 
 constexpr int BT_MAX_INST = 512;  // instances of a launch of k_batch_tma at most
@@ -89,21 +113,119 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
+// ---- wall tiles.  `cw` is the stage one row into the taller windows, so
+// that a node of tile row ly pulls from window row ly + 1 and a node of ring
+// row ry (0: below the tile, H + 1: above it) from row ry, as in the interior
+// body; the node's own population of plane j sits at row (pull row + e_jy).
+
+// Half-way bounce-back (reading A3) of one node, lane LANE of g: every
+// population whose source (ax - e_ix, ay - e_iy) lies outside the nx x ny
+// grid becomes the node's own opposite population, staged at window row
+// pr - e_iy and column wx of that plane, with the lid term on the links from
+// above a moving top wall (the operations of pull9, in its order).
+template <typename S, int PE, int BW, int LANE, typename V>
+__device__ __forceinline__ void bounce_node(const S *cw, int pr, int wx, int ax, int ay, int nx, int ny, bool lid_on,
+                                            float lid, V g[9])
+{
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        const int sx = ax - ex_of(i), sy = ay - ey_of(i);
+        if ((sx < 0) | (sx >= nx) | (sy < 0) | (sy >= ny)) {
+            float v = Pair<S>::one(cw + opp_of(i) * PE + (pr - ey_of(i)) * BW + wx);
+            if (sy >= ny && lid_on) {
+                if (i == 7) v -= lid;
+                if (i == 8) v += lid;
+            }
+            if constexpr (std::is_same<V, float>::value) g[i] = v;
+            else if (LANE == 0) g[i].v.x = v;
+            else g[i].v.y = v;
+        }
+    }
+}
+
+// Wall-aware pulls of the node pair (ax, ay), (ax + 1, ay) at window row pr,
+// column wx of its first node (nodes past the grid get values never stored).
+template <typename S, int PE, int BW>
+__device__ __forceinline__ void pull_pair_wall(const S *cw, int pr, int wx, int ax, int ay, int nx, int ny,
+                                               bool lid_on, float lid, F2 g[9])
+{
+    pull_pair<S, PE>(cw + pr * BW + wx, g);
+    if ((ax <= 0) | (ax + 2 >= nx) | (ay <= 0) | (ay + 1 >= ny)) {
+        bounce_node<S, PE, BW, 0>(cw, pr, wx, ax, ay, nx, ny, lid_on, lid, g);
+        bounce_node<S, PE, BW, 1>(cw, pr, wx + 1, ax + 1, ay, nx, ny, lid_on, lid, g);
+    }
+}
+
+// Density of one ring unit of a wall tile at (x0, y0) (the units of
+// ring_density), formed only where the unit's node lies inside the grid: the
+// gradients never read a position outside it.
+template <typename S, int W, int H, int PE, int BW, int RW, int PADX>
+__device__ __forceinline__ void ring_density_wall(int tid, const S *cw, float *Rs, int x0, int y0, int nx, int ny,
+                                                  bool lid_on, float lid)
+{
+    constexpr int PAIRS = W / 2;
+    if (tid < 2 * PAIRS) {
+        const int ry = tid < PAIRS ? 0 : H + 1;
+        const int rx = 2 * (tid < PAIRS ? tid : tid - PAIRS);
+        const int ax = x0 + rx, ay = y0 - 1 + ry;
+        if ((ax >= nx) | (ay < 0) | (ay >= ny)) return;
+        F2 gr[9];
+        pull_pair_wall<S, PE, BW>(cw, ry, rx + PADX, ax, ay, nx, ny, lid_on, lid, gr);
+        *reinterpret_cast<float2 *>(Rs + ry * RW + rx + 2) = sum9(gr).v;
+    } else {
+        const int c = tid - 2 * PAIRS;
+        const int ry = c >> 1, lx = (c & 1) ? W : -1;
+        const int ax = x0 + lx, ay = y0 - 1 + ry;
+        if ((ax < 0) | (ax >= nx) | (ay < 0) | (ay >= ny)) return;
+        const S *b = cw + ry * BW + lx + PADX;
+        float gr[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) gr[i] = Pair<S>::one(b + i * PE - ex_of(i));
+        bounce_node<S, PE, BW, 0>(cw, ry, lx + PADX, ax, ay, nx, ny, lid_on, lid, gr);
+        Rs[ry * RW + lx + 2] = sum9(gr);
+    }
+}
+
+// Density gradients (reading A1) of the node (ax, ay) at tile position
+// (lx, ly), its neighbours' positions clamped into the grid (the stencil and
+// operation order of general_tile).
+template <int RW>
+__device__ __forceinline__ void node_gradients_clamped(const float *Rs, int lx, int ly, int ax, int ay, int nx, int ny,
+                                                       float i12, float i12r, float &dxr, float &dyr)
+{
+    const int xc = lx + 2, xw = (ax > 0 ? lx - 1 : lx) + 2, xe = (ax + 1 < nx ? lx + 1 : lx) + 2;
+    const int yc = (ly + 1) * RW, ys = (ay > 0 ? ly : ly + 1) * RW, yn = (ay + 1 < ny ? ly + 2 : ly + 1) * RW;
+    const float rE = Rs[yc + xe], rW = Rs[yc + xw];
+    const float rN = Rs[yn + xc], rS = Rs[ys + xc];
+    const float rNE = Rs[yn + xe], rNW = Rs[yn + xw];
+    const float rSE = Rs[ys + xe], rSW = Rs[ys + xw];
+    drho_stencil<float>(rE, rW, rN, rS, rNE, rNW, rSE, rSW, i12, i12r, dxr, dyr);
+}
+
+template <typename S>
+struct Scalar;
+template <>
+struct Scalar<float> {
+    static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
+};
+template <>
+struct Scalar<__half> {
+    static __device__ __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
 template <typename S>
 __global__ void __launch_bounds__(BT_THREADS, 2)
 k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restrict__ coefs, BatchDyn *dyn, int ninst,
-            int total_itiles, int total_etiles, double2 *partials, BatchCtl *ctl, int steps)
+            int total_tiles, double2 *partials, BatchCtl *ctl, int steps)
 {
     using C = BatchTmaCfg<S>;
     constexpr int W = C::W, H = C::H;
-    static_assert(C::NQ == 1, "one node pair per thread");
+    static_assert(H * C::PAIRS == BT_THREADS, "one node pair per thread");
     constexpr int PE = C::PLANE_BYTES / (int)sizeof(S);  // plane stride in elements
     constexpr int RF = C::R_BYTES / (int)sizeof(float);  // floats per density tile
     constexpr int RING = 2 * C::PAIRS + 2 * C::RH;        // ring units
     constexpr int CB = (int)sizeof(BatchCoef<float>);
     static_assert(RING <= BT_THREADS - 32, "one ring unit per thread at most, none in the producer's warp");
-    static_assert(C::R_BYTES >= srho_floats(BT_THREADS) * (int)sizeof(float), "density tile too small for the strips");
-    static_assert(C::R_BYTES >= PAIR_SRHO * (int)sizeof(float), "density tile too small for the pair tiles");
     static_assert(CB % 16 == 0 && C::STAGE_BYTES % 128 == 0 && C::R_BYTES % 128 == 0, "16-byte bulk copies");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -128,47 +250,50 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
     __syncthreads();
     uint32_t ph = 0;  // bit b: parity of the next completion of bar[b]
 
-    // The CTA's interior tiles are the global list strided by the grid size,
-    // so that neighbouring tiles are staged at about the same time by
-    // neighbouring CTAs and their shared window rows and columns come from
-    // L2.  The producer thread (lane 0 of the last warp, which has no ring
-    // work and would otherwise wait at the tile barrier) walks them: it finds
-    // the next tile before the barrier and, right after it, issues the tile's
-    // nine window copies into the freed stage and one bulk copy of its
-    // instance's coefficients, both completing on the stage's barrier.
+    // The CTA's tiles are the global list strided by the grid size, so that
+    // neighbouring tiles are staged at about the same time by neighbouring
+    // CTAs and their shared window rows and columns come from L2.  The
+    // producer thread (lane 0 of the last warp, which has no ring work and
+    // would otherwise wait at the tile barrier) walks them: it finds the next
+    // tile before the barrier and, right after it, issues the tile's nine
+    // window copies into the freed stage and one bulk copy of its instance's
+    // coefficients, both completing on the stage's barrier.
     const bool producer = tid == BT_THREADS - 32;
     int nq = 0, wi = 0;
     auto pick = [&]() {
         BatchTile r;
         r.q = -1;
-        while (nq < total_itiles) {
-            while (wi + 1 < ninst && nq >= tinst[wi + 1].itile_start) wi++;  // tiles are in instance order
+        while (nq < total_tiles) {
+            while (wi + 1 < ninst && nq >= tinst[wi + 1].tile_start) wi++;  // tiles are in instance order
             const BatchTileInst &e = tinst[wi];
             const int q = nq;
             nq += gridDim.x;
             if (!e.active) continue;
-            const int lt = q - e.itile_start;
+            const int lt = q - e.tile_start;
             const int ty = lt / e.ntx;
             r.q = q;
             r.i = wi;
             r.t = e.t;
-            r.ox = C::PADX + (lt - ty * e.ntx) * W;  // interior origin (PADX, 2), see make_batch_tma_plan
-            r.oy = 2 + ty * H;
-            r.x0 = min(r.ox, e.xlast);
-            r.y0 = min(r.oy, e.ylast);
+            r.x0 = (lt - ty * e.ntx) * W;
+            r.y0 = ty * H;
+            // interior: every node of the tile and of its ring at least one
+            // node inside the walls (their pulls need no bounce-back)
+            r.wall = !((r.x0 >= 2) & (r.x0 + W + 2 <= e.nx) & (r.y0 >= 2) & (r.y0 + H + 2 <= e.ny));
             break;
         }
         return r;
     };
+    auto tmap_of = [&](const BatchTile &r) { return tinst[r.i].tmap + 2 * r.wall + (int)(r.t & 1); };
     auto issue = [&](int st, const BatchTile &r, int cb) {
         rec[st] = r;
         if (r.q >= 0) {
             const BatchTileInst &e = tinst[r.i];
             S *stg = st ? stage1 : stage0;
-            const CUtensorMap *map = e.tmap + (int)(r.t & 1);
-            mbar_arrive_expect_tx(&bar[st], 9u * C::BOX_BYTES + CB);
+            const CUtensorMap *map = tmap_of(r);
+            mbar_arrive_expect_tx(&bar[st], 9u * (r.wall ? C::BOXW_BYTES : C::BOX_BYTES) + CB);
+            const int yb = r.y0 - 1 - r.wall;  // first window row for e_y = 0
 #pragma unroll
-            for (int i = 0; i < 9; i++) tma_load_3d(stg + i * PE, map, &bar[st], r.x0 - C::PADX, r.y0 - 1 - ey_of(i), i);
+            for (int i = 0; i < 9; i++) tma_load_3d(stg + i * PE, map, &bar[st], r.x0 - C::PADX, yb - ey_of(i), i);
             bulk_load(cstage + cb, coefs + e.slot, CB, &bar[st]);
         }
     };
@@ -181,17 +306,17 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
             BatchTileInst e;
             e.tmap = I.tmap;
             e.t = I.t0 + s;
-            e.itile_start = I.itile_start;
-            e.ntx = I.in.ntx;
-            e.xlast = I.in.xlast;
-            e.ylast = I.in.ylast;
+            e.tile_start = I.tile_start;
+            e.ntx = I.tiles_x;
+            e.nx = I.gd.nx;
+            e.ny = I.gd.ny;
             e.slot = I.slot;
             e.active = ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && e.t < I.max_steps;
-            e.etile_start = I.etile_start;
+            e.lid_on = I.gd.lid_on;
+            e.pad = 0;
             tinst[k] = e;
         }
         __syncthreads();
-        // ---- interior tiles, TMA-staged
         // producer: the tile after the two in flight, picked one tile early so
         // that its descriptor is prefetched by the time its copies are issued
         BatchTile nxt;
@@ -202,7 +327,7 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
             issue(0, pick(), 0);
             issue(1, pick(), 1);
             nxt = pick();
-            if (nxt.q >= 0) prefetch_tmap(tinst[nxt.i].tmap + (int)(nxt.t & 1));
+            if (nxt.q >= 0) prefetch_tmap(tmap_of(nxt));
         }
         __syncthreads();  // the first two records
         for (int it = 0;; it++) {
@@ -211,30 +336,48 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
             // barrier, and the rewrite becomes visible at the next tile's barrier
             const BatchTile r = rec[st];
             if (r.q < 0) break;  // no later record holds a tile either
+            const BatchTileInst &e = tinst[r.i];
             // read now, used after the collision: the loads overlap the wait and the pulls
             const BatchInst &I = inst[r.i];
             const bool epi = ((r.t + 1) % 20) == 0;
-            const bool own = (r.x0 + x >= r.ox) & (r.y0 + ly >= r.oy);
+            const int nx = e.nx, ny = e.ny;
+            const int ax = r.x0 + x, ay = r.y0 + ly;  // this thread's first node
+            const bool v0 = (ax < nx) & (ay < ny), v1 = (ax + 1 < nx) & (ay < ny);
             float *snap = static_cast<float *>(I.snap);
             S *dst = static_cast<S *>(I.pop[(int)(r.t & 1) ^ 1]);
             const long long plane = I.gd.plane;
-            const long long o = (long long)(r.y0 + ly) * I.gd.pitch + (r.x0 + x);
+            const long long o = (long long)ay * I.gd.pitch + ax;
             float2 snv = make_float2(0.f, 0.f);
-            if (epi && own) snv = __ldcs(reinterpret_cast<const float2 *>(snap + o));
+            if (epi) {
+                if (v1) snv = __ldcs(reinterpret_cast<const float2 *>(snap + o));
+                else if (v0) snv.x = __ldcs(snap + o);
+            }
             const S *cur = st ? stage1 : stage0;
             float *Rs = R + st * RF;
+            // the coefficients staged with this tile (buffer it mod BT_CBUF)
+            const BatchCoef<float> &K = cstage[it & (BT_CBUF - 1)];
             // a thread whose wait runs out still pulls (stale shared memory) so
             // that every thread reaches the barrier, which takes the vote
             const bool ok = mbar_wait_bounded(&bar[st], (ph >> st) & 1u);
             ph ^= 1u << st;
             F2 g[9];
-            pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
-            *reinterpret_cast<float2 *>(Rs + (ly + 1) * C::RW + x + 2) = sum9(g).v;
-            if (tid < RING) ring_density<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cur, Rs);
+            if (!r.wall) {  // uniform across the CTA: one tile per CTA at a time
+                pull_pair<S, PE>(cur + (ly + 1) * C::BW + x + C::PADX, g);
+                *reinterpret_cast<float2 *>(Rs + (ly + 1) * C::RW + x + 2) = sum9(g).v;
+                if (tid < RING) ring_density<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cur, Rs);
+            } else {
+                const S *cw = cur + C::BW;
+                const bool lid_on = e.lid_on != 0;
+                pull_pair_wall<S, PE, C::BW>(cw, ly + 1, x + C::PADX, ax, ay, nx, ny, lid_on, K.k.lid, g);
+                *reinterpret_cast<float2 *>(Rs + (ly + 1) * C::RW + x + 2) = sum9(g).v;
+                if (tid < RING)
+                    ring_density_wall<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cw, Rs, r.x0, r.y0, nx, ny, lid_on,
+                                                                           K.k.lid);
+            }
             BatchTile nn;  // producer: the tile after nxt
             if (producer) {
                 nn = pick();
-                if (nn.q >= 0) prefetch_tmap(tinst[nn.i].tmap + (int)(nn.t & 1));
+                if (nn.q >= 0) prefetch_tmap(tmap_of(nn));
             }
             if (__syncthreads_or(!ok)) {
                 if (producer) {
@@ -244,71 +387,46 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
                 }
                 return;
             }
-            // the coefficients staged with this tile (buffer it mod BT_CBUF)
-            const BatchCoef<float> &K = cstage[it & (BT_CBUF - 1)];
             if (producer) {  // every pull from this stage is done
                 issue(st, nxt, (it + 2) & (BT_CBUF - 1));
                 nxt = nn;
             }
             F2 dxr, dyr;
-            pair_gradients<C::RW>(Rs + (ly + 1) * C::RW + x + 2, K.k.inv12, K.k.inv12r, dxr, dyr);
+            if (!r.wall || ((ax >= 1) & (ax + 2 < nx) & (ay >= 1) & (ay + 1 < ny))) {
+                pair_gradients<C::RW>(Rs + (ly + 1) * C::RW + x + 2, K.k.inv12, K.k.inv12r, dxr, dyr);
+            } else {
+                dxr = F2(0.f);
+                dyr = F2(0.f);
+                if (v0) node_gradients_clamped<C::RW>(Rs, x, ly, ax, ay, nx, ny, K.k.inv12, K.k.inv12r, dxr.v.x, dyr.v.x);
+                if (v1)
+                    node_gradients_clamped<C::RW>(Rs, x + 1, ly, ax + 1, ay, nx, ny, K.k.inv12, K.k.inv12r, dxr.v.y,
+                                                  dyr.v.y);
+            }
             F2 ux, uy, drho;
             collide<F2, true, false>(K.k2, g, dxr, dyr, ux, uy, drho);
+            if (v1) {
 #pragma unroll
-            for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * plane + o, g[i]);
+                for (int i = 0; i < 9; i++) Pair<S>::store(dst + (long long)i * plane + o, g[i]);
+            } else if (v0) {
+#pragma unroll
+                for (int i = 0; i < 9; i++) Scalar<S>::store(dst + (long long)i * plane + o, g[i].v.x);
+            }
             if (epi) {  // uniform across the CTA: one instance per tile
                 RedAcc<float> acc;
-                if (own) {
+                if (v1) {
                     __stcs(reinterpret_cast<float2 *>(snap + o), ux.v);
                     const float da = ux.v.x - snv.x, db = ux.v.y - snv.y;
                     acc.add(da * da, drho.v.x);
                     acc.add(db * db, drho.v.y);
+                } else if (v0) {
+                    __stcs(snap + o, ux.v.x);
+                    const float da = ux.v.x - snv.x;
+                    acc.add(da * da, drho.v.x);
                 }
                 double a, b;
                 acc.block_total(a, b, red);
-                if (tid == 0) partials[I.part_base + (r.q - I.itile_start)] = make_double2(a, b);
+                if (tid == 0) partials[I.part_base + (r.q - I.tile_start)] = make_double2(a, b);
                 __syncthreads();  // red is reused by the next total
-            }
-        }
-        // ---- edge strips: general tile body, L2-coherent loads, density tile
-        // in R; the CTA's edge tiles strided over the global edge-tile list
-        // (their instances found in the shared table, not in global memory)
-        {
-            int ei = 0;
-            for (int e = blockIdx.x; e < total_etiles; e += gridDim.x) {
-                while (ei + 1 < ninst && e >= tinst[ei + 1].etile_start) ei++;
-                if (!tinst[ei].active) continue;
-                const BatchInst &I = inst[ei];
-                const long long t = tinst[ei].t;
-                const int le = e - I.etile_start;
-                const S *src = static_cast<const S *>(I.pop[(int)(t & 1)]);
-                S *dst = static_cast<S *>(I.pop[(int)(t & 1) ^ 1]);
-                float *snap = static_cast<float *>(I.snap);
-                const BatchCoef<float> &K = coefs[I.slot];
-                const bool epi = ((t + 1) % 20) == 0;
-                RedAcc<float> acc;
-                if (I.in.ntx == 0) {
-                    // a grid without interior tiles: the 64 x 8 node-pair tiles of
-                    // the general kernel (what a single handle runs on it)
-                    const int x0 = (le % I.tiles_x) * PTW, y0 = (le / I.tiles_x) * PTH;
-                    if (epi) pair_tile<S, true, true, false, true, false>(src, dst, I.gd, K.k, K.k2, snap, x0, y0, acc, R);
-                    else pair_tile<S, true, false, false, true, false>(src, dst, I.gd, K.k, K.k2, snap, x0, y0, acc, R);
-                } else {
-                    int ex0, ey0, ex1, ey1, lw;
-                    rect_tile(I.edge, le, ex0, ey0, ex1, ey1, lw);
-                    if (epi)
-                        general_tile<S, float, true, true, false, true>(src, dst, I.gd, K.k, snap, ex0, ey0, ex1, ey1,
-                                                                        lw, acc, R);
-                    else
-                        general_tile<S, float, true, false, false, true>(src, dst, I.gd, K.k, snap, ex0, ey0, ex1, ey1,
-                                                                         lw, acc, R);
-                }
-                if (epi) {
-                    double a, b;
-                    acc.block_total(a, b, red);
-                    if (tid == 0) partials[I.part_base + I.in.ntx * I.in.nty + le] = make_double2(a, b);
-                    __syncthreads();  // red is reused by the next total
-                }
             }
         }
         if (!grid_barrier(ctl)) return;

@@ -346,8 +346,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                         const float rN = c[RW], rS = c[-RW];
                         const float rNE = c[RW + 1], rNW = c[RW - 1];
                         const float rSE = c[-RW + 1], rSW = c[-RW - 1];
-                        dx[j] = (float(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
-                        dy[j] = (float(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+                        drho_stencil<float>(rE, rW, rN, rS, rNE, rNW, rSE, rSW, k.inv12, k.inv12r, dx[j], dy[j]);
                     }
                 }
                 F2 ux, uy, drho;
@@ -477,8 +476,7 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
                     const T rN = c[RW], rS = c[-RW];
                     const T rNE = c[RW + 1], rNW = c[RW - 1];
                     const T rSE = c[-RW + 1], rSW = c[-RW - 1];
-                    dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
-                    dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+                    drho_stencil<T>(rE, rW, rN, rS, rNE, rNW, rSE, rSW, k.inv12, k.inv12r, dxr, dyr);
                 }
                 T ux, uy, drho;
                 collide<T, DRHO, FORCE, RAW>(k, g, dxr, dyr, ux, uy, drho);

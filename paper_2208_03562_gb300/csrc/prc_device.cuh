@@ -158,6 +158,18 @@ PRC_HD T sum9(const T g[9])
     return vadd(vadd(g[0], d58), vadd(p13, p24));
 }
 
+// Density gradients of reading A1 from the eight neighbour densities,
+// dx = [4 (rE - rW) + (rNE - rNW) + (rSE - rSW)] / 12 and
+// dy = [4 (rN - rS) + (rNE - rSE) + (rNW - rSW)] / (12 r), in a fixed sequence
+// of explicitly rounded operations, so that every kernel (scalar or packed
+// lanes) forms the same value for a node.
+template <typename T>
+PRC_HD void drho_stencil(T rE, T rW, T rN, T rS, T rNE, T rNW, T rSE, T rSW, T i12, T i12r, T &dx, T &dy)
+{
+    dx = vmul(vadd(vfma(splat<T>(4.0), vsub(rE, rW), vsub(rNE, rNW)), vsub(rSE, rSW)), i12);
+    dy = vmul(vadd(vfma(splat<T>(4.0), vsub(rN, rS), vsub(rNE, rSE)), vsub(rNW, rSW)), i12r);
+}
+
 // The collision in deviation form (App. A with the algebra rearranged as in
 // the file header), generic over float, double and packed F2.
 // In: g[9] streamed shifted populations, density gradient (dxr, dyr).

@@ -114,37 +114,6 @@ inline Plan make_plan(const lbm_params &p, int num_sms, int variant)
     return pl;
 }
 
-// Interior tiling and edge strips of the batch engine's TMA-staged body
-// (k_batch_tma: BT_W x BT_H tiles at least two nodes from every wall, x origin
-// 16-byte aligned; the rest in strips of the general tile body for CTAs of
-// BT_THREADS).  A grid too small for one interior tile is all strip: in.ntx =
-// in.nty = 0 and one rectangle over the whole grid.  The same rules as
-// make_plan's for the single-instance interior kernel.
-inline void make_batch_tma_plan(const lbm_params &p, int padx, prc::Interior &in, prc::Rects &edge)
-{
-    std::memset(&in, 0, sizeof(in));
-    std::memset(&edge, 0, sizeof(edge));
-    const int W = prc::BT_W, H = prc::BT_H, threads = prc::BT_THREADS;
-    const int ix0 = padx, iy0 = 2;
-    if (p.model == LBM_MODEL_PRC && p.nx - 2 - ix0 >= W && p.ny - 2 - iy0 >= H) {
-        const int xlast = ((p.nx - 2 - W) / padx) * padx;
-        const int ylast = p.ny - 2 - H;
-        const int xend = xlast + W, yend = ylast + H;
-        in.ix0 = ix0;
-        in.iy0 = iy0;
-        in.ntx = ceil_div(xend - ix0, W);
-        in.nty = ceil_div(yend - iy0, H);
-        in.xlast = xlast;
-        in.ylast = ylast;
-        add_strip(edge, 0, 0, p.nx, iy0, threads);
-        add_strip(edge, 0, yend, p.nx, p.ny, threads);
-        add_strip(edge, 0, iy0, ix0, yend, threads);
-        add_strip(edge, xend, iy0, p.nx, yend, threads);
-    } else {
-        add_strip(edge, 0, 0, p.nx, p.ny, threads);
-    }
-}
-
 // cuTensorMapEncodeTiled, looked up once through the runtime's driver entry
 // points (null when unavailable).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,

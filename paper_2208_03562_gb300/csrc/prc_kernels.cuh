@@ -92,8 +92,7 @@ __device__ __forceinline__ void general_tile(const S *__restrict__ src, S *__res
         const T rN = c[RW], rS = c[-RW];
         const T rNE = c[RW + 1], rNW = c[RW - 1];
         const T rSE = c[-RW + 1], rSW = c[-RW - 1];
-        dxr = (T(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * k.inv12;
-        dyr = (T(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * k.inv12r;
+        drho_stencil<T>(rE, rW, rN, rS, rNE, rNW, rSE, rSW, k.inv12, k.inv12r, dxr, dyr);
         __syncthreads();  // srho may be refilled by the next tile of this CTA
     }
 

@@ -87,13 +87,13 @@ struct DtypeOps {
     cudaError_t (*cluster_launch)(const void *pop0, const void *pop1, const Grid &gd, const Coef<double> &k,
                                   void *snap, DevStatus *st, long long t0, int n, int nc, int rpc, int smem,
                                   bool drho, bool force, cudaStream_t s);
-    // batch engine with TMA-staged interior tiles (k_batch_tma; FP32 / FP16
+    // batch engine with TMA-staged tiles (k_batch_tma; FP32 / FP16
     // storage, null for FP64): shared-memory opt-in (once, outside any stream
     // capture), resident CTAs per SM, one cooperative launch
     cudaError_t (*batch_tma_prepare)();
     cudaError_t (*batch_tma_occupancy)(int *blocks_per_sm);
-    cudaError_t (*batch_tma_launch)(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int itiles,
-                                    int etiles, double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s);
+    cudaError_t (*batch_tma_launch)(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int tiles,
+                                    double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s);
 };
 
 extern const DtypeOps ops_f64, ops_f32, ops_f16;

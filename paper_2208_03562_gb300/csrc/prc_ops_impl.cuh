@@ -317,13 +317,13 @@ cudaError_t op_batch_tma_occupancy(int *blocks_per_sm)
 }
 
 template <typename TT>
-cudaError_t op_batch_tma_launch(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int itiles,
-                                int etiles, double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s)
+cudaError_t op_batch_tma_launch(const BatchInst *inst, const void *coefs, BatchDyn *dyn, int ninst, int tiles,
+                                double2 *partials, BatchCtl *ctl, int steps, int grid, cudaStream_t s)
 {
     if constexpr (std::is_same<TT, float>::value) {
         const BatchCoef<float> *cf = static_cast<const BatchCoef<float> *>(coefs);
-        void *args[] = {(void *)&inst, (void *)&cf, (void *)&dyn, (void *)&ninst, (void *)&itiles, (void *)&etiles,
-                        (void *)&partials, (void *)&ctl, (void *)&steps};
+        void *args[] = {(void *)&inst, (void *)&cf, (void *)&dyn, (void *)&ninst, (void *)&tiles, (void *)&partials,
+                        (void *)&ctl, (void *)&steps};
         return cudaLaunchCooperativeKernel((const void *)k_batch_tma<S>, dim3(grid), dim3(BT_THREADS), args,
                                            batch_tma_smem<S>(), s);
     }

@@ -145,8 +145,7 @@ __device__ __forceinline__ void pair_tile(const S *__restrict__ src, S *__restri
             const float rN = c[RW], rS = c[-RW];
             const float rNE = c[RW + 1], rNW = c[RW - 1];
             const float rSE = c[-RW + 1], rSW = c[-RW - 1];
-            dx[j] = (float(4) * (rE - rW) + (rNE - rNW) + (rSE - rSW)) * kf.inv12;
-            dy[j] = (float(4) * (rN - rS) + (rNE - rSE) + (rNW - rSW)) * kf.inv12r;
+            drho_stencil<float>(rE, rW, rN, rS, rNE, rNW, rSE, rSW, kf.inv12, kf.inv12r, dx[j], dy[j]);
         }
         dxr = F2(dx[0], dx[1]);
         dyr = F2(dy[0], dy[1]);

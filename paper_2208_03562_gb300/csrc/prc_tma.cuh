@@ -198,10 +198,8 @@ __device__ __forceinline__ void pair_gradients(const float *c, float i12, float 
                  SR = *reinterpret_cast<const float2 *>(c - RW + 2);
     // node x: E = M.y, W = L.y, N = NM.x, S = SM.x, NE = NM.y, NW = NL.y, SE = SM.y, SW = SL.y
     // node x+1: E = Rr.x, W = M.x, N = NM.y, S = SM.y, NE = NR.x, NW = NM.x, SE = SR.x, SW = SM.x
-    dxr = F2((4.f * (M.y - L.y) + (NM.y - NL.y) + (SM.y - SL.y)) * i12,
-             (4.f * (Rr.x - M.x) + (NR.x - NM.x) + (SR.x - SM.x)) * i12);
-    dyr = F2((4.f * (NM.x - SM.x) + (NM.y - SM.y) + (NL.y - SL.y)) * i12r,
-             (4.f * (NM.y - SM.y) + (NR.x - SR.x) + (NM.x - SM.x)) * i12r);
+    drho_stencil<F2>(F2(M.y, Rr.x), F2(L.y, M.x), F2(NM.x, NM.y), F2(SM.x, SM.y), F2(NM.y, NR.x), F2(NL.y, NM.x),
+                     F2(SM.y, SR.x), F2(SL.y, SM.x), F2(i12), F2(i12r), dxr, dyr);
 }
 
 // Persistent step kernel: the interior tiles, NQ pairs of neighbouring nodes

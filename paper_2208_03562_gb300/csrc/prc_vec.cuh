@@ -27,10 +27,34 @@ template <> __host__ __device__ inline F2 from_double<F2>(double x) { return F2(
 // the collision can be exercised off the GPU by developer tooling.
 #define PRC_HD __host__ __device__ __forceinline__
 
-// ---- scalar float
-PRC_HD float vadd(float a, float b) { return a + b; }
-PRC_HD float vsub(float a, float b) { return a - b; }
-PRC_HD float vmul(float a, float b) { return a * b; }
+// ---- scalar float.  On the device every operation is rounded on its own
+// (the compiler may not fuse a product into a following sum), so that a node
+// computed in a scalar lane gets bitwise what the same node gets in a packed
+// FP32x2 lane, whose operations are never fused either.
+PRC_HD float vadd(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+PRC_HD float vsub(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+PRC_HD float vmul(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
 PRC_HD float vfma(float a, float b, float c)
 {
 #ifdef __CUDA_ARCH__

@@ -294,10 +294,13 @@ def test_specialised_kernel_equals_single_instances(dtype):
         h.close()
 
 
-# nx, ny, r, gamma, nu, u_lid: several interior tiles both ways with a shifted
-# last tile column and row (300 x 100, 200 x 90, 517 x 211), a single interior
-# tile row or column (134 x 26, 72 x 12 and 70 x 19 in FP32; the last two have
-# none in FP16, whose tile origins align to 8 nodes), no interior tile (33 x 40)
+# nx, ny, r, gamma, nu, u_lid: grids whose single-handle interior kernel has
+# several interior tiles both ways with a shifted last tile column and row
+# (300 x 100, 200 x 90, 517 x 211), a single interior tile row or column
+# (134 x 26, 72 x 12 and 70 x 19 in FP32; the last two have none in FP16, whose
+# tile origins align to 8 nodes), or none (33 x 40); in the batch body they
+# cover tiles clear of the walls, wall tiles on every side and corner, odd
+# widths (517, 33) and last rows and columns reaching past the grid
 TMA_CASES = [
     (300, 100, 0.5, 0.3, 0.01, 0.03),
     (200, 90, 2.0, 0.1, 0.01, 0.02),
@@ -322,13 +325,15 @@ def batch_tile_variant(dtype):
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_tma_body_equals_single_instances_on_the_interior_kernel(dtype, use_graph):
     """The TMA-staged batch body runs, per node, what a single handle runs on
-    the interior kernel with the same 64 x 8 tile: the staged pulls, the density ring, the
-    gradients and the packed collision in its interior tiles, the general
-    tile body on its edge strips, the node-pair tiles of the general kernel
-    on grids without interior tiles.  Every slot's populations must equal
-    that handle's bitwise, with the step counts; the residual and mass sum
-    the same node terms grouped by tile instead of by CTA, so they agree to
-    FP64 round-off."""
+    the interior kernel with the same 64 x 8 tile: the staged pulls, the
+    density ring, the gradients and the packed collision in tiles clear of
+    the walls, and in tiles at a wall the wall-aware pulls from the taller
+    staged windows, ring densities inside the grid and clamped gradients,
+    where the handle takes the general tile body on its edge strips (and on
+    the whole of a grid without interior tiles).  Every slot's populations
+    must equal that handle's bitwise, with the step counts; the residual and
+    mass sum the same node terms grouped by tile instead of by CTA, so they
+    agree to FP64 round-off."""
     b = L.Batch(len(TMA_CASES), dtype)
     slots, refs = [], []
     for k, (nx, ny, r, gamma, nu, u) in enumerate(TMA_CASES):
