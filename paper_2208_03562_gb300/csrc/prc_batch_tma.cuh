@@ -14,13 +14,13 @@
 //     same pulls, density ring, gradients and packed FP32x2 collision.
 //   * Any other tile (a wall tile) takes windows two rows taller (one more
 //     row below and above), which hold, for every node of the tile and of its
-//     ring, both its pulls and all nine of its own populations.  Streaming is
-//     then wall-aware from shared memory: a source outside the grid is
-//     replaced by the node's own opposite population, with the moving-lid
-//     term on the two diagonal links from above the top wall (half-way
-//     bounce-back, reading A3).  Ring nodes inside the grid form their
-//     density the same way; the density gradient reads its eight neighbours
-//     at positions clamped into the grid (the nearest fluid node's density
+//     ring, both its pulls and all nine of its own populations.  One pass
+//     copies, for each node at a wall, its own opposite populations into the
+//     out-of-grid window cells that its pulls across the wall read (ghost
+//     cells), so that the plain pulls stream with half-way bounce-back; the
+//     moving-lid term is added to the two diagonal links of the top row
+//     (reading A3).  The density gradient reads its eight neighbours at
+//     positions clamped into the grid (the nearest fluid node's density
 //     beyond a wall, reading A1); only nodes inside the grid are stored.
 // Every node computes what the general tile body computes for it (the same
 // pulls, density sums, stencil and collision, in the same order), so an
@@ -116,72 +116,108 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // ---- wall tiles.  `cw` is the stage one row into the taller windows, so
 // that a node of tile row ly pulls from window row ly + 1 and a node of ring
 // row ry (0: below the tile, H + 1: above it) from row ry, as in the interior
-// body; the node's own population of plane j sits at row (pull row + e_jy).
+// body; a node at absolute row y sits in the window of plane p at row
+// y - y0 + 1 + e_py (relative to cw).
 
-// Half-way bounce-back (reading A3) of one node, lane LANE of g: every
-// population whose source (ax - e_ix, ay - e_iy) lies outside the nx x ny
-// grid becomes the node's own opposite population, staged at window row
-// pr - e_iy and column wx of that plane, with the lid term on the links from
-// above a moving top wall (the operations of pull9, in its order).
-template <typename S, int PE, int BW, int LANE, typename V>
-__device__ __forceinline__ void bounce_node(const S *cw, int pr, int wx, int ax, int ay, int nx, int ny, bool lid_on,
-                                            float lid, V g[9])
+// Ghost cells of a wall tile (half-way bounce-back, reading A3): for every
+// node n of the tile or its ring that lies inside the grid and every
+// population i whose source n - e_i lies beyond a wall, the window of plane i
+// at n - e_i -- a position outside the grid, which the copy filled with zeros
+// and which no other pull reads -- receives the node's own population
+// opp(i), so that the plain pulls then stream with bounce-back.  The cells of
+// one wall are those of its nodes (one column or row of the tile and ring)
+// and of the three populations that point away from it; a corner cell is
+// written twice with the same value.  The moving-lid term is added after
+// the pull, in the collision precision (lid_pull).  All threads take part;
+// the caller synchronises before the pulls.
+template <typename S, int W, int H, int PE, int BW, int PADX, int THREADS>
+__device__ __forceinline__ void fill_ghosts(S *cw, int tid, int x0, int y0, int nx, int ny)
 {
-#pragma unroll
-    for (int i = 1; i < 9; i++) {
-        const int sx = ax - ex_of(i), sy = ay - ey_of(i);
-        if ((sx < 0) | (sx >= nx) | (sy < 0) | (sy >= ny)) {
-            float v = Pair<S>::one(cw + opp_of(i) * PE + (pr - ey_of(i)) * BW + wx);
-            if (sy >= ny && lid_on) {
-                if (i == 7) v -= lid;
-                if (i == 8) v += lid;
-            }
-            if constexpr (std::is_same<V, float>::value) g[i] = v;
-            else if (LANE == 0) g[i].v.x = v;
-            else g[i].v.y = v;
+    constexpr int NV = (H + 2) * 3, NH = (W + 2) * 3;  // cells of a vertical / horizontal wall
+    const bool wl = x0 == 0, wr = (nx - 1 >= x0 - 1) & (nx - 1 <= x0 + W);
+    const bool wb = y0 == 0, wt = (ny - 1 >= y0 - 1) & (ny - 1 <= y0 + H);
+    const int total = (wl ? NV : 0) + (wr ? NV : 0) + (wb ? NH : 0) + (wt ? NH : 0);
+    bool wrote = false;
+    for (int c = tid; c < total; c += THREADS) {
+        int k = c, side;  // 0 left, 1 right, 2 bottom, 3 top
+        const int n0 = wl ? NV : 0, n1 = wr ? NV : 0, n2 = wb ? NH : 0;
+        if (k < n0) {
+            side = 0;
+        } else if ((k -= n0) < n1) {
+            side = 1;
+        } else if ((k -= n1) < n2) {
+            side = 2;
+        } else {
+            k -= n2;
+            side = 3;
         }
+        const int sel = k % 3, along = k / 3;
+        int ax, ay, i;
+        if (side < 2) {
+            ax = side == 0 ? 0 : nx - 1;
+            ay = y0 - 1 + along;
+            i = side == 0 ? (sel == 0 ? 1 : (sel == 1 ? 5 : 8)) : (sel == 0 ? 3 : (sel == 1 ? 6 : 7));
+        } else {
+            ax = x0 - 1 + along;
+            ay = side == 2 ? 0 : ny - 1;
+            i = side == 2 ? (sel == 0 ? 2 : (sel == 1 ? 5 : 6)) : (sel == 0 ? 4 : (sel == 1 ? 7 : 8));
+        }
+        if ((ax < 0) | (ax >= nx) | (ay < 0) | (ay >= ny)) continue;
+        // e_i and the opposite direction, for i in 1..8 (Eq. 3 ordering)
+        const int exi = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+        const int eyi = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+        const int j = i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5;
+        const int col = ax - x0 + PADX, row = ay - y0 + 1;
+        cw[i * PE + row * BW + col - exi] = cw[j * PE + (row - eyi) * BW + col];
+        wrote = true;
     }
+    // the next copies into this stage (async proxy) come after these writes
+    if (wrote) fence_async_shared();
 }
 
-// Wall-aware pulls of the node pair (ax, ay), (ax + 1, ay) at window row pr,
-// column wx of its first node (nodes past the grid get values never stored).
-template <typename S, int PE, int BW>
-__device__ __forceinline__ void pull_pair_wall(const S *cw, int pr, int wx, int ax, int ay, int nx, int ny,
-                                               bool lid_on, float lid, F2 g[9])
+// The moving-lid term of the pulls from above the top wall (the two
+// diagonal links SW and SE of a node in the top row, reading A3), added to
+// the bounced populations in the collision precision as pull9 does.
+template <typename V>
+__device__ __forceinline__ void lid_pull(V g[9], float lid);
+template <>
+__device__ __forceinline__ void lid_pull<float>(float g[9], float lid)
 {
-    pull_pair<S, PE>(cw + pr * BW + wx, g);
-    if ((ax <= 0) | (ax + 2 >= nx) | (ay <= 0) | (ay + 1 >= ny)) {
-        bounce_node<S, PE, BW, 0>(cw, pr, wx, ax, ay, nx, ny, lid_on, lid, g);
-        bounce_node<S, PE, BW, 1>(cw, pr, wx + 1, ax + 1, ay, nx, ny, lid_on, lid, g);
-    }
+    g[7] -= lid;
+    g[8] += lid;
+}
+template <>
+__device__ __forceinline__ void lid_pull<F2>(F2 g[9], float lid)
+{
+    g[7].v.x -= lid;
+    g[7].v.y -= lid;
+    g[8].v.x += lid;
+    g[8].v.y += lid;
 }
 
-// Density of one ring unit of a wall tile at (x0, y0) (the units of
-// ring_density), formed only where the unit's node lies inside the grid: the
-// gradients never read a position outside it.
+// Density of one ring unit of a wall tile (the units of ring_density) from
+// the ghost-filled windows, with the lid term for a unit in the top row.
+// Units outside the grid form values that the clamped gradients never read.
 template <typename S, int W, int H, int PE, int BW, int RW, int PADX>
-__device__ __forceinline__ void ring_density_wall(int tid, const S *cw, float *Rs, int x0, int y0, int nx, int ny,
-                                                  bool lid_on, float lid)
+__device__ __forceinline__ void ring_density_wall(int tid, const S *cw, float *Rs, int y0, int ny, bool lid_on,
+                                                  float lid)
 {
     constexpr int PAIRS = W / 2;
     if (tid < 2 * PAIRS) {
         const int ry = tid < PAIRS ? 0 : H + 1;
         const int rx = 2 * (tid < PAIRS ? tid : tid - PAIRS);
-        const int ax = x0 + rx, ay = y0 - 1 + ry;
-        if ((ax >= nx) | (ay < 0) | (ay >= ny)) return;
         F2 gr[9];
-        pull_pair_wall<S, PE, BW>(cw, ry, rx + PADX, ax, ay, nx, ny, lid_on, lid, gr);
+        pull_pair<S, PE>(cw + ry * BW + rx + PADX, gr);
+        if (lid_on & (y0 - 1 + ry == ny - 1)) lid_pull(gr, lid);
         *reinterpret_cast<float2 *>(Rs + ry * RW + rx + 2) = sum9(gr).v;
     } else {
         const int c = tid - 2 * PAIRS;
         const int ry = c >> 1, lx = (c & 1) ? W : -1;
-        const int ax = x0 + lx, ay = y0 - 1 + ry;
-        if ((ax < 0) | (ax >= nx) | (ay < 0) | (ay >= ny)) return;
         const S *b = cw + ry * BW + lx + PADX;
         float gr[9];
 #pragma unroll
         for (int i = 0; i < 9; i++) gr[i] = Pair<S>::one(b + i * PE - ex_of(i));
-        bounce_node<S, PE, BW, 0>(cw, ry, lx + PADX, ax, ay, nx, ny, lid_on, lid, gr);
+        if (lid_on & (y0 - 1 + ry == ny - 1)) lid_pull(gr, lid);
         Rs[ry * RW + lx + 2] = sum9(gr);
     }
 }
@@ -366,13 +402,15 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
                 *reinterpret_cast<float2 *>(Rs + (ly + 1) * C::RW + x + 2) = sum9(g).v;
                 if (tid < RING) ring_density<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cur, Rs);
             } else {
-                const S *cw = cur + C::BW;
+                S *cw = (st ? stage1 : stage0) + C::BW;
                 const bool lid_on = e.lid_on != 0;
-                pull_pair_wall<S, PE, C::BW>(cw, ly + 1, x + C::PADX, ax, ay, nx, ny, lid_on, K.k.lid, g);
+                fill_ghosts<S, W, H, PE, C::BW, C::PADX, BT_THREADS>(cw, tid, r.x0, r.y0, nx, ny);
+                __syncthreads();  // every ghost cell of the stage is written
+                pull_pair<S, PE>(cw + (ly + 1) * C::BW + x + C::PADX, g);
+                if (lid_on & (ay == ny - 1)) lid_pull(g, K.k.lid);
                 *reinterpret_cast<float2 *>(Rs + (ly + 1) * C::RW + x + 2) = sum9(g).v;
                 if (tid < RING)
-                    ring_density_wall<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cw, Rs, r.x0, r.y0, nx, ny, lid_on,
-                                                                           K.k.lid);
+                    ring_density_wall<S, W, H, PE, C::BW, C::RW, C::PADX>(tid, cw, Rs, r.y0, ny, lid_on, K.k.lid);
             }
             BatchTile nn;  // producer: the tile after nxt
             if (producer) {
