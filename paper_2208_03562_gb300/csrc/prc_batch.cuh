@@ -296,7 +296,7 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
         // ---- one time step of every active instance
         int i = 0;
         int ci = -1;         // instance whose state and counter were read last (they change only between steps)
-        bool active = false;
+        bool active = false, epi = false;
         long long t = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             while (i + 1 < ninst && tile >= inst[i + 1].tile_start) i++;  // tiles are in instance order
@@ -308,9 +308,9 @@ k_batch(const BatchInst *__restrict__ inst, const BatchCoef<T> *__restrict__ coe
                 // CTA takes one decision for all its threads
                 t = I.t0 + s;
                 active = __syncthreads_and(ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && t < I.max_steps);
+                epi = ((t + 1) % 20) == 0;
             }
             if (!active) continue;
-            const bool epi = ((t + 1) % 20) == 0;
             if constexpr (SPEC == 1) {
                 if (epi) batch_tile_t<S, T, true, true, false, false>(I, coefs[I.slot], (int)(t & 1), tile - I.tile_start,
                                                                    partials, bsm);

@@ -63,12 +63,13 @@ struct BatchTmaCfg {
 // stores by every CTA, made visible by the grid barrier).
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// A staged tile: global tile index (-1: none), instance, step count of the
-// instance, origin, and whether it is a wall tile.
+// A staged tile: global tile index (-1: none), instance, origin, whether it
+// is a wall tile, the parity of the instance's step count (its source set)
+// and whether the step is one of the instance's residual steps.
 struct BatchTile {
     int q, i;
-    long long t;
     int x0, y0, wall;
+    int par, epi;
 };
 
 // What the tile walk needs of an instance, copied into shared memory at the
@@ -77,9 +78,9 @@ struct BatchTile {
 // memory for it.
 struct BatchTileInst {
     const CUtensorMap *tmap;  // [interior box: set 0, set 1; wall box: set 0, set 1]
-    long long t;              // the instance's step count in this step
     int tile_start, ntx, nx, ny;
-    int slot, active, lid_on, pad;
+    int slot, active, lid_on;
+    int par, epi;  // the instance's step count in this step: parity, and whether it ends a residual interval
 };
 
 constexpr int BT_MAX_INST = 512;  // instances of a launch of k_batch_tma at most
@@ -309,7 +310,8 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
             const int ty = lt / e.ntx;
             r.q = q;
             r.i = wi;
-            r.t = e.t;
+            r.par = e.par;
+            r.epi = e.epi;
             r.x0 = (lt - ty * e.ntx) * W;
             r.y0 = ty * H;
             // interior: every node of the tile and of its ring at least one
@@ -319,7 +321,7 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
         }
         return r;
     };
-    auto tmap_of = [&](const BatchTile &r) { return tinst[r.i].tmap + 2 * r.wall + (int)(r.t & 1); };
+    auto tmap_of = [&](const BatchTile &r) { return tinst[r.i].tmap + 2 * r.wall + r.par; };
     auto issue = [&](int st, const BatchTile &r, int cb) {
         rec[st] = r;
         if (r.q >= 0) {
@@ -340,16 +342,17 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
         for (int k = tid; k < ninst; k += BT_THREADS) {
             const BatchInst &I = inst[k];
             BatchTileInst e;
+            const long long t = I.t0 + s;
             e.tmap = I.tmap;
-            e.t = I.t0 + s;
+            e.par = (int)(t & 1);
+            e.epi = (t + 1) % 20 == 0;
             e.tile_start = I.tile_start;
             e.ntx = I.tiles_x;
             e.nx = I.gd.nx;
             e.ny = I.gd.ny;
             e.slot = I.slot;
-            e.active = ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && e.t < I.max_steps;
+            e.active = ld_relaxed_i32(&dyn[I.slot].state) == BATCH_ACTIVE && t < I.max_steps;
             e.lid_on = I.gd.lid_on;
-            e.pad = 0;
             tinst[k] = e;
         }
         __syncthreads();
@@ -375,12 +378,12 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
             const BatchTileInst &e = tinst[r.i];
             // read now, used after the collision: the loads overlap the wait and the pulls
             const BatchInst &I = inst[r.i];
-            const bool epi = ((r.t + 1) % 20) == 0;
+            const bool epi = r.epi != 0;
             const int nx = e.nx, ny = e.ny;
             const int ax = r.x0 + x, ay = r.y0 + ly;  // this thread's first node
             const bool v0 = (ax < nx) & (ay < ny), v1 = (ax + 1 < nx) & (ay < ny);
             float *snap = static_cast<float *>(I.snap);
-            S *dst = static_cast<S *>(I.pop[(int)(r.t & 1) ^ 1]);
+            S *dst = static_cast<S *>(I.pop[r.par ^ 1]);
             const long long plane = I.gd.plane;
             const long long o = (long long)ay * I.gd.pitch + ax;
             float2 snv = make_float2(0.f, 0.f);

@@ -297,9 +297,10 @@ k_cluster(const S *__restrict__ pop0, const S *__restrict__ pop1, Grid gd, Coef<
     int done = 0;
     bool waited = false;  // the last cluster barrier phase has been waited on
     const double nnodes = (double)gd.nx * (double)gd.ny;
-    for (; done < nsteps; done++) {
+    int t20 = (int)((t0 + 1) % 20);  // index of the step being made, modulo 20
+    for (; done < nsteps; done++, t20 = t20 == 19 ? 0 : t20 + 1) {
         const long long t = t0 + done + 1;  // absolute index of the step being made
-        const bool epi = (t % 20) == 0;
+        const bool epi = t20 == 0;
         v.own = b ? own1 : own0;
         v.own_cta = b ? own1c : own0c;
         v.prev = b ? prev1 : prev0;
