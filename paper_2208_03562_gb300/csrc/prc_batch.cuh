@@ -92,6 +92,7 @@ struct BatchCtl {
     int error;           // 1: barrier timeout
     int hold;            // failure-detection check: CTA 0 withholds its first arrival
     long long limit;     // wait limit of the grid barrier in SM clock cycles (0: about two seconds)
+    unsigned long long claim;  // tile claims of k_batch_tma, counted over the launch
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)

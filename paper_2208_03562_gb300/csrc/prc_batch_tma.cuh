@@ -26,7 +26,8 @@
 // pulls, density sums, stencil and collision, in the same order), so an
 // instance's populations are bitwise those of a single handle on the 64 x 8
 // interior-kernel variant, whose edge strips take the general tile body.
-// The CTAs take the global tile list strided by the grid size; in each, one
+// The CTAs take the global tile list strided by the grid size for about 7/8
+// of it and claim the rest from a counter; in each, one
 // producer thread walks its tiles two ahead, skips the tiles of retired
 // instances, stages each tile's windows and its instance's coefficients, and
 // hands the tile to the CTA through a record in shared memory that the tile's
@@ -287,28 +288,57 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
     __syncthreads();
     uint32_t ph = 0;  // bit b: parity of the next completion of bar[b]
 
-    // The CTA's tiles are the global list strided by the grid size, so that
-    // neighbouring tiles are staged at about the same time by neighbouring
-    // CTAs and their shared window rows and columns come from L2.  The
-    // producer thread (lane 0 of the last warp, which has no ring work and
-    // would otherwise wait at the tile barrier) walks them: it finds the next
+    // Tile assignment.  A CTA first takes its tiles statically, strided by the
+    // grid size (blockIdx.x, + grid, + 2 grid, ...: neighbouring tiles are
+    // staged at about the same time by neighbouring CTAs, and their shared
+    // window rows and columns come from L2), NS of them, about 7/8 of an
+    // equal share; the remaining tiles, from NS grid on, are claimed one at a
+    // time from a launch-wide counter, so that a CTA that ran ahead takes
+    // more of them.  With fixed equal shares the CTAs of a large launch
+    // waited at each step's grid barrier for 8-14 % of the time; claiming
+    // every tile measured slower than this split (an atomic per tile), and
+    // claiming the last quarter no better.  Claim numbers of step s start at
+    // s (D + grid), D = max(0, tiles - NS grid): each CTA makes exactly one
+    // claim past the end (the one that ends its step), so a step takes
+    // D + grid claims.  One claim is always in flight: the next is requested
+    // as soon as the previous is taken, a tile ahead of its use.  The producer
+    // thread (lane 0 of the last warp, which has no ring work and would
+    // otherwise wait at the tile barrier) walks the tiles: it finds the next
     // tile before the barrier and, right after it, issues the tile's nine
     // window copies into the freed stage and one bulk copy of its instance's
     // coefficients, both completing on the stage's barrier.
     const bool producer = tid == BT_THREADS - 32;
-    int nq = 0, wi = 0;
+    const int G = gridDim.x;
+    const int NS = max(3, total_tiles / G - max(2, total_tiles / (8 * G)));
+    const long long dyn_tiles = total_tiles > NS * G ? (long long)total_tiles - (long long)NS * G : 0;
+    int wi = 0, nstatic = 0;
+    bool ended = false;
+    unsigned long long kp = 0;  // the claim in flight
+    long long base = 0;         // first claim number of this step
     auto pick = [&]() {
         BatchTile r;
         r.q = -1;
-        while (nq < total_tiles) {
-            while (wi + 1 < ninst && nq >= tinst[wi + 1].tile_start) wi++;  // tiles are in instance order
+        for (;;) {
+            long long q;
+            if (nstatic < NS) {
+                q = blockIdx.x + (long long)nstatic * G;
+                nstatic = q < total_tiles ? nstatic + 1 : NS;
+                if (q >= total_tiles) continue;
+            } else {
+                if (ended) break;
+                q = (long long)NS * G + ((long long)kp - base);
+                if (q >= total_tiles) {
+                    ended = true;
+                    break;
+                }
+                kp = atomicAdd(&ctl->claim, 1ULL);
+            }
+            while (wi + 1 < ninst && q >= tinst[wi + 1].tile_start) wi++;  // tiles are in instance order
             const BatchTileInst &e = tinst[wi];
-            const int q = nq;
-            nq += gridDim.x;
             if (!e.active) continue;
-            const int lt = q - e.tile_start;
+            const int lt = (int)q - e.tile_start;
             const int ty = lt / e.ntx;
-            r.q = q;
+            r.q = (int)q;
             r.i = wi;
             r.par = e.par;
             r.epi = e.epi;
@@ -361,7 +391,10 @@ k_batch_tma(const BatchInst *__restrict__ inst, const BatchCoef<float> *__restri
         BatchTile nxt;
         if (producer) {
             fence_proxy_async_global();
-            nq = blockIdx.x;
+            base = (long long)s * (dyn_tiles + G);
+            kp = atomicAdd(&ctl->claim, 1ULL);  // taken after the static tiles
+            nstatic = 0;
+            ended = false;
             wi = 0;
             issue(0, pick(), 0);
             issue(1, pick(), 1);
