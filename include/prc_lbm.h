@@ -314,8 +314,9 @@ lbm_status lbm_step_noalloc(const lbm_params *p, const void *src, void *dst, voi
  * active slot with ONE persistent cooperative kernel launch (through a
  * captured CUDA graph when use_graph != 0): each step sweeps the tiles of
  * all active slots (64 x 8 nodes in pairs for FP32 / FP16 storage, 32 x 8 for
- * FP64) with the wall-aware fused update of the general kernel, a bounded grid
- * barrier separates the steps, and every slot evaluates its FP64 residual on
+ * FP64) with the wall-aware fused update (the tile body is chosen as
+ * lbm_batch_set_body describes), a bounded grid barrier separates the steps,
+ * and every slot evaluates its FP64 residual on
  * its own step counter (every 20 steps, Sec. 5.2).  A slot retires on the
  * device as soon as its residual is below its tolerance (CONVERGED), is not
  * finite (DIVERGED) or it reached its step limit (MAXSTEPS); the others
