@@ -364,6 +364,49 @@ def test_tma_body_equals_single_instances_on_the_interior_kernel(dtype, use_grap
         h.close()
 
 
+# nx, ny, r, gamma, nu, u_lid: grids no larger than a tile or two, where every
+# tile of the TMA-staged batch body is a wall tile: the smallest grid, a tile
+# row shorter than the 8-row tile, odd widths, one exact tile, one node past it
+TINY_CASES = [
+    (3, 3, 1.0, 0.5, 0.02, 0.03),
+    (5, 7, 1.6, 0.2, 0.005, 0.01),
+    (9, 4, 0.5, 1.0, 0.01, 0.02),
+    (64, 8, 0.25, 0.3, 0.01, 0.02),
+    (65, 9, 2.0, 0.6, 0.02, 0.05),
+    (130, 17, 1.0, 0.1, 0.01, 0.02),
+]
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F16])
+def test_tma_body_on_grids_of_a_tile_or_less(dtype):
+    """Wall tiles on every side of one tile at once (ghost cells of all four
+    walls and their corners in one window, rows and columns past the grid):
+    each slot of the TMA-staged body equals a single handle bitwise."""
+    b = L.Batch(len(TINY_CASES), dtype)
+    slots, refs = [], []
+    for k, (nx, ny, r, gamma, nu, u) in enumerate(TINY_CASES):
+        p = L.lbm_params_init(nx, ny, r, gamma, nu, u, dtype)
+        w = S.rest_weights(S.OracleParams(nx=nx, ny=ny, r=r, gamma=gamma, nu=nu, u_lid=u))
+        f0 = w[:, None, None] + I.noise(3700 + k, (9, ny, nx), 1e-3)
+        s = b.add(p, 0.0, 10 ** 6)
+        b.set_populations(s, f0)
+        h = L.Lbm(p)
+        h.variant = batch_tile_variant(dtype)
+        h.set_populations(f0)
+        slots.append(s)
+        refs.append(h)
+    assert b.tma_body
+    for n in (1, 19, 40):  # crossing residual steps
+        b.run(n)
+        for s, h in zip(slots, refs):
+            h.step(n)
+            info, st = b.query(s)
+            assert st == L.SLOT_ACTIVE and info.step == h.info().step
+            assert np.array_equal(b.populations(s), h.populations()), (b.shapes[s], info.step)
+    for h in refs:
+        h.close()
+
+
 def test_tma_body_retires_where_single_handles_stop():
     """Retirement on the residual with the TMA-staged body: each slot stops at
     the step where a single handle on the interior kernel stops, with the
