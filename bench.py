@@ -562,9 +562,13 @@ def batch_summary(cavs, per, wall_s):
     for st, _, _, _ in per:
         states[st] = states.get(st, 0) + 1
     agg = ns / wall_s / 1e9
+    peak, kind = peak_hbm()
     out = {"workload": "%d cavities, nx 64..1024, ny 32..512, r in {0.25,0.5,1,2}, gamma 0.05..1, Re 100..5000, "
                        "FP32, residual 1e-7 (seed 0)" % n,
-           "aggregate_glups": agg, "wall_s": wall_s, "states": states,
+           "aggregate_glups": agg,
+           "hbm_frac": {"value": agg * BYTES_PER_NODE["f32"] / peak, "peak_gbs": peak, "peak_kind": kind,
+                        "what": "aggregate node updates x 72 B (FP32 algorithmic bytes) / HBM copy bandwidth"},
+           "wall_s": wall_s, "states": states,
            "retired_fraction": (n - states.get("ACTIVE", 0)) / n}
     if states.get("ACTIVE", 0):
         rem = sum(left * c.nodes for (st, _, _, left), c in zip(per, cavs) if st == "ACTIVE" and left is not None)
